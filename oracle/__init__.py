@@ -1,0 +1,199 @@
+"""FP64 CPU oracle for the localized style-transfer loss and gradient.
+
+TEST INFRASTRUCTURE ONLY: only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline leg
+may import this package. The library under test (``paper_2212_13459_gb300``) never imports it and
+shares no code with it; the only shared module is the seeded input generator ``synth``.
+
+Contents:
+* ``nst_oracle.c`` (compiled with gcc, OpenMP): VGG-19 to ReLU5_1, Gram/content losses, Table 1
+  feature gradients, the hand-written reverse pass, and Algorithm 1 (blocks with margins).
+* ``lbfgs.py``: L-BFGS two-loop recursion and the dense inverse-BFGS matrix it must equal.
+* ``bicubic.py``: x2 bicubic upscaling (the initialisation step of Algorithm 2).
+
+Pins of this oracle against things other than itself live in tests/test_oracle_*.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nst_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+NSTYLE = 5
+STYLE_CONVS = [0, 2, 4, 8, 12]
+STYLE_CHANNELS = [64, 128, 256, 512, 512]
+STYLE_STRIDES = [1, 2, 4, 8, 16]
+CONTENT_CONV = 9
+CONV_COUT = [64, 64, 128, 128, 256, 256, 256, 256, 512, 512, 512, 512, 512]
+CONV_STRIDE = [1, 1, 2, 2, 4, 4, 4, 4, 8, 8, 8, 8, 16]
+
+
+def build(force: bool = False) -> str:
+    """Compile nst_oracle.c into _build/liboracle.so (plain gcc, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c11", _SRC,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.orc_param_count.restype = ctypes.c_long
+            L.orc_features.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_style_grams.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_content_target.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_loss_grad.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                        ctypes.c_double, dp, dp, dp, dp]
+            L.orc_loss_grad_tiled.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                              ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+            L.orc_table1_gram.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                          dp, dp]
+            L.orc_table1_mse.argtypes = [dp, dp, ctypes.c_long, ctypes.c_double, dp, dp]
+            L.orc_plan_1d.argtypes = [ctypes.c_int, ctypes.c_int, ip]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError("oracle error %d" % rc)
+
+
+def pack_params(params) -> np.ndarray:
+    """[(W, b)] * 13 (any float dtype) -> one float64 vector in the oracle's parameter order."""
+    v = np.concatenate([np.concatenate([np.asarray(w, np.float64).ravel(),
+                                        np.asarray(b, np.float64).ravel()]) for w, b in params])
+    assert v.size == lib().orc_param_count()
+    return np.ascontiguousarray(v)
+
+
+def _img(x):
+    x = np.ascontiguousarray(np.asarray(x, np.float64))
+    assert x.ndim == 3 and x.shape[0] == 3
+    return x
+
+
+def features(P, x, conv):
+    x = _img(x)
+    H, W = x.shape[1:]
+    s = CONV_STRIDE[conv]
+    out = np.zeros((CONV_COUT[conv], H // s, W // s))
+    _check(lib().orc_features(_p(P), _p(x), H, W, conv, _p(out)))
+    return out
+
+
+def style_grams(P, v):
+    """G^L(v) for L in L_s, as a list of 5 square float64 arrays."""
+    v = _img(v)
+    H, W = v.shape[1:]
+    tot = sum(c * c for c in STYLE_CHANNELS)
+    out = np.zeros(tot)
+    _check(lib().orc_style_grams(_p(P), _p(v), H, W, _p(out)))
+    return split_grams(out)
+
+
+def split_grams(flat):
+    res, o = [], 0
+    for c in STYLE_CHANNELS:
+        res.append(flat[o:o + c * c].reshape(c, c).copy())
+        o += c * c
+    return res
+
+
+def join_grams(gs):
+    return np.ascontiguousarray(np.concatenate([np.asarray(g, np.float64).ravel() for g in gs]))
+
+
+def content_target(P, u):
+    u = _img(u)
+    H, W = u.shape[1:]
+    out = np.zeros((512, H // 8, W // 8))
+    _check(lib().orc_content_target(_p(P), _p(u), H, W, _p(out)))
+    return out
+
+
+def loss_grad(P, x, content_t, style_G, w_style, lambda_c, want_grad=True):
+    """Untiled E(x) and dE/dx. Returns (E, grad or None, parts[6], grams[5])."""
+    x = _img(x)
+    H, W = x.shape[1:]
+    ct = np.ascontiguousarray(content_t, np.float64)
+    sg = join_grams(style_G)
+    ws = np.ascontiguousarray(w_style, np.float64)
+    E = np.zeros(1)
+    parts = np.zeros(6)
+    grams = np.zeros(sg.size)
+    grad = np.zeros((3, H, W)) if want_grad else None
+    _check(lib().orc_loss_grad(_p(P), _p(x), H, W, _p(ct), _p(sg), _p(ws), float(lambda_c),
+                               _p(E), _p(grad), _p(parts), _p(grams)))
+    return float(E[0]), grad, parts, split_grams(grams)
+
+
+def loss_grad_tiled(P, x, content_t, style_G, w_style, lambda_c, tiles, margins,
+                    want_grad=True):
+    """Algorithm 1 with a tiles[0] x tiles[1] partition and margins (step 1, step 2)."""
+    x = _img(x)
+    H, W = x.shape[1:]
+    ct = np.ascontiguousarray(content_t, np.float64)
+    sg = join_grams(style_G)
+    ws = np.ascontiguousarray(w_style, np.float64)
+    E = np.zeros(1)
+    parts = np.zeros(6)
+    grams = np.zeros(sg.size)
+    grad = np.zeros((3, H, W)) if want_grad else None
+    _check(lib().orc_loss_grad_tiled(_p(P), _p(x), H, W, _p(ct), _p(sg), _p(ws),
+                                     float(lambda_c), int(tiles[0]), int(tiles[1]),
+                                     int(margins[0]), int(margins[1]), _p(E), _p(grad),
+                                     _p(parts), _p(grams)))
+    return float(E[0]), grad, parts, split_grams(grams)
+
+
+def table1_gram(V, Gref, w):
+    V = np.ascontiguousarray(V, np.float64)
+    npx, nc = V.shape
+    Gref = np.ascontiguousarray(Gref, np.float64)
+    E = np.zeros(1)
+    g = np.zeros_like(V)
+    lib().orc_table1_gram(_p(V), npx, nc, _p(Gref), float(w), _p(E), _p(g))
+    return float(E[0]), g
+
+
+def table1_mse(V, Vref, lam):
+    V = np.ascontiguousarray(V, np.float64)
+    Vref = np.ascontiguousarray(Vref, np.float64)
+    E = np.zeros(1)
+    g = np.zeros_like(V)
+    lib().orc_table1_mse(_p(V), _p(Vref), V.size, float(lam), _p(E), _p(g))
+    return float(E[0]), g
+
+
+def plan_1d(L, k):
+    b = (ctypes.c_int * (k + 1))()
+    rc = lib().orc_plan_1d(int(L), int(k), b)
+    _check(rc)
+    return list(b)

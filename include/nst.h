@@ -1,0 +1,156 @@
+/*
+ * nst.h -- C ABI of libnst: the localized style-transfer loss and its image gradient on one GB300
+ * (Galerne et al., "Scaling Painting Style Transfer", arXiv 2212.13459).
+ *
+ * Conventions for every call:
+ *   - Images are float32, planar 3 x H x W (RGB, row-major, C-contiguous), in device memory unless
+ *     the name ends in _host. The caller owns them; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Every device call
+ *     is asynchronous on that stream unless stated; its inputs must stay valid until the stream
+ *     reaches the work.
+ *   - Argument errors are returned synchronously (NST_ERR_INVALID_ARG, NST_ERR_SHAPE,
+ *     NST_ERR_STATE). Errors detected on the device (a bounded wait that ran out, a non-finite
+ *     input) are latched in a device word; nst_sync_status() synchronizes the stream and returns
+ *     it. No C++ exception crosses this boundary. nst_last_error() gives a message.
+ *   - A context is bound to the device that was current at nst_create(); calls must come from a
+ *     thread whose current device is that device. Calls on one context must not overlap.
+ */
+#ifndef NST_H
+#define NST_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nst_ctx nst_ctx;
+typedef struct nst_lbfgs nst_lbfgs;
+
+typedef enum {
+  NST_OK = 0,
+  NST_ERR_INVALID_ARG = 1, /* null pointer, bad enum, negative size */
+  NST_ERR_SHAPE = 2,       /* image smaller than 16 x 16, or a tile grid that does not fit */
+  NST_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed (message in nst_last_error) */
+  NST_ERR_OOM = 4,         /* device allocation failed */
+  NST_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out (kernel returned early) */
+  NST_ERR_NONFINITE = 6,   /* the image x held a NaN or Inf */
+  NST_ERR_STATE = 7        /* call order violated (e.g. loss before targets) */
+} nst_status;
+
+enum { NST_PREC_FP32 = 0, NST_PREC_BF16 = 1 };
+enum { NST_CONV_AUTO = 0, NST_CONV_SIMT = 1, NST_CONV_TC = 2 };
+
+/* Run-time configuration.
+ *   w_style[5]: w_L of the Gram loss at ReLU1_1..ReLU5_1 (Section 3.1, Eq. 3).
+ *   lambda_c:   content weight (Section 3.1); the content loss is the unnormalised squared
+ *               distance of ReLU4_2 features.
+ *   tiles_h, tiles_w: the block partition of Section 4.1 given as a k_h x k_w grid; inner block
+ *               boundaries lie on multiples of 16 px so every block shares the image's pooling grid.
+ *   margin1, margin2: block margins in px (multiples of 16) for Step 1 and Step 2 of Algorithm 1.
+ *               The paper uses 256 for both; 80 and 160 cover the ReLU5_1 receptive field
+ *               (forward reach 70 px, gradient reach 155 px) and give the same result.
+ *   precision:  NST_PREC_FP32 (FP32 storage, FP32 CUDA-core convolutions) or NST_PREC_BF16
+ *               (BF16 storage, tcgen05 tensor-core convolutions with FP32 accumulation).
+ *   conv_engine: NST_CONV_AUTO (tcgen05 for BF16, SIMT for FP32) or a forced engine (SIMT works
+ *               for both precisions; TC needs BF16).
+ *   max_batch_tiles: tiles processed per launch (0 = all tiles of the pass, within
+ *               workspace_limit_bytes).
+ *   workspace_limit_bytes: device workspace cap for activations of a tile batch (0 = 64 GiB). */
+typedef struct {
+  float w_style[5];
+  float lambda_c;
+  int tiles_h, tiles_w;
+  int margin1, margin2;
+  int precision;
+  int conv_engine;
+  int max_batch_tiles;
+  long long workspace_limit_bytes;
+} nst_config;
+
+/* Fill *cfg with the defaults: w_style = 0.2 each, lambda_c = 1e-3, 1 x 1 tiles, margins 80/160,
+ * BF16, auto engine, auto batching. Host only. */
+nst_status nst_config_default(nst_config *cfg);
+
+/* Create a context on the current device. params_host: float32 host array of n_params values,
+ * for conv l = conv1_1..conv5_1 in order: W_l[Cout][Cin][3][3] then b_l[Cout] (VGG-19 up to
+ * ReLU5_1, Section 3.1; n_params = 12,944,960). The weights are copied; the caller keeps
+ * ownership of params_host. */
+nst_status nst_create(nst_ctx **out, const float *params_host, long long n_params,
+                      const nst_config *cfg);
+nst_status nst_destroy(nst_ctx *ctx);
+
+/* Style statistics G^L(v), L in {ReLU_k_1}, of the style image v (3 x Hv x Wv, device), computed
+ * block by block with Step 1 of Algorithm 1 (Require line of Algorithm 1). Stored in the context
+ * (FP64). */
+nst_status nst_style_targets(nst_ctx *ctx, const float *v_dev, int Hv, int Wv, void *stream);
+
+/* Content target V^{ReLU4_2}(u) of the content image u (3 x H x W, device), computed block by
+ * block (Require line of Algorithm 1). Stored in the context at the path's precision; fixes the
+ * image size H x W for nst_loss_grad. */
+nst_status nst_content_targets(nst_ctx *ctx, const float *u_dev, int H, int W, void *stream);
+
+/* One evaluation of Algorithm 1: E(x) = E_content + sum_L w_L ||G^L(x) - G^L(v)||_F^2 (Eq. 1-3) and
+ * grad = dE/dx, by two passes over the blocks. x_dev and grad_dev are 3 x H x W float32 device
+ * arrays (H x W must match nst_content_targets); grad_dev is fully overwritten. loss_dev: one
+ * double in device memory, or NULL. Requires both targets. */
+nst_status nst_loss_grad(nst_ctx *ctx, const float *x_dev, int H, int W, float *grad_dev,
+                         double *loss_dev, void *stream);
+
+/* Same evaluation from host memory: copies x_host to the device, evaluates, copies the gradient
+ * and the loss back, and synchronizes the stream before returning. x_host and grad_host should
+ * be page-locked for full copy speed. loss_host may be NULL. */
+nst_status nst_loss_grad_host(nst_ctx *ctx, const float *x_host, int H, int W, float *grad_host,
+                              double *loss_host, void *stream);
+
+/* Statistics of the last completed nst_loss_grad (synchronizes the stream first):
+ * parts_host[6] = the five Gram terms w_L ||G^L(x) - G^L(v)||^2 and the content term;
+ * grams_host (may be NULL) = G^L(x) for the five style layers, concatenated row-major
+ * (64^2 + 128^2 + 256^2 + 512^2 + 512^2 = 610,304 doubles). */
+nst_status nst_get_stats(nst_ctx *ctx, double *parts_host, double *grams_host, void *stream);
+
+/* The stored style Gram matrices G^L(v) (same layout as grams_host above). Synchronizes. */
+nst_status nst_get_style_grams(nst_ctx *ctx, double *grams_host, void *stream);
+
+/* Per-kernel-class device time of the last nst_loss_grad when timing is enabled
+ * (nst_set_timing), in milliseconds, and algorithmic FLOP counts of the tensor-core / SIMT
+ * convolutions it ran: out[0] = conv ms, out[1] = conv FLOPs, out[2] = gram ms, out[3] = other
+ * ms, out[4] = conv launches, out[5] = total kernel launches. Synchronizes. */
+nst_status nst_get_timing(nst_ctx *ctx, double *out6, void *stream);
+nst_status nst_set_timing(nst_ctx *ctx, int enable);
+
+/* Synchronize `stream` and return (then clear) the latched device status. */
+nst_status nst_sync_status(nst_ctx *ctx, void *stream);
+
+/* Message for the last error on ctx (or the last context-free error if ctx is NULL). */
+const char *nst_last_error(nst_ctx *ctx);
+
+/* The block partition used by the library (host only): rects_out receives tiles_h*tiles_w
+ * entries of 8 ints {iy0, iy1, ix0, ix1, ey0, ey1, ex0, ex1} (inner and extended rectangles for
+ * `margin`), row-major over the tile grid. */
+nst_status nst_tile_plan(int H, int W, int tiles_h, int tiles_w, int margin, int *rects_out);
+
+/* ---- L-BFGS (Section 3.1; history sizes of Section 5.1) --------------------------------------
+ * Two-loop recursion over the m newest pairs, H0 = gamma I with gamma = s^T y / y^T y, pairs
+ * with y^T s <= 1e-10 skipped, no line search: step 1 except min(1, 1/||g||_1) on the first
+ * iteration. FP32 vectors, FP64 dot products, all on the device (no host round trip).
+ * State (history 2 m n floats) is owned by the nst_lbfgs object, allocated at create. */
+nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m);
+nst_status nst_lbfgs_destroy(nst_lbfgs *st);
+/* One iteration: given x (device, n floats, updated in place) and g = grad E(x) (device), form
+ * the new pair from the previous call, compute d = -H g and set x <- x + t d. */
+nst_status nst_lbfgs_step(nst_lbfgs *st, float *x_dev, const float *g_dev, void *stream);
+/* Number of pairs currently stored and iterations taken (host ints; synchronizes). */
+nst_status nst_lbfgs_info(nst_lbfgs *st, int *pairs, long long *iters, void *stream);
+
+/* ---- multiscale initialisation (Algorithm 2, "upscale current x by a factor 2") -------------
+ * Bicubic (Keys a = -0.75, half-pixel centres, clamped borders) resampling of x_small
+ * (3 x h x w, device) to x (3 x H x W, device). */
+nst_status nst_upsample_init(const float *x_small_dev, int h, int w, float *x_dev, int H, int W,
+                             void *stream);
+
+/* Library version string. */
+const char *nst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NST_H */

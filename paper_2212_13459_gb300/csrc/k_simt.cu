@@ -1,0 +1,704 @@
+// k_simt.cu -- CUDA-core kernels of the localized loss/gradient path:
+//   * the plain FP32 convolution engine (implicit GEMM on CUDA cores, no TF32), used by the FP32
+//     form of the path and as a cross-check of the tensor-core engine;
+//   * conv1_1 forward straight from the caller's planar image (block gather fused) and conv1_1
+//     input-gradient with the inner-part scatter into dE/dx fused (Algorithm 1, last step);
+//   * 2x2 max pooling and its adjoint (argmax routing + ReLU gate);
+//   * split Gram partial sums over owned pixels and their FP64 reduction (Eq. 4, Algorithm 1
+//     Step 1), the style finalisation (Eq. 3 and Table 1 row 2), the content loss over owned
+//     pixels (Algorithm 1 Step 2), the content-target crop, and a finiteness check.
+#include "nst_internal.cuh"
+#include "nst_kernels.h"
+
+namespace nst {
+
+// ---- vector helpers ----------------------------------------------------------------------------
+__device__ __forceinline__ void load4(const float *p, float v[4]) {
+  float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16 *p, float v[4]) {
+  uint2 t = *reinterpret_cast<const uint2 *>(p);
+  __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162 *>(&t.x);
+  __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&t.y);
+  float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+}
+__device__ __forceinline__ void store4(float *p, const float v[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16 *p, const float v[4]) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 t;
+  t.x = *reinterpret_cast<unsigned *>(&a);
+  t.y = *reinterpret_cast<unsigned *>(&b);
+  *reinterpret_cast<uint2 *>(p) = t;
+}
+__device__ __forceinline__ void load8(const float *p, float v[8]) { load4(p, v); load4(p + 4, v + 4); }
+__device__ __forceinline__ void load8(const __nv_bfloat16 *p, float v[8]) {
+  uint4 t = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&t);
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    float2 f = __bfloat1622float2(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void store8(float *p, const float v[8]) { store4(p, v); store4(p + 4, v + 4); }
+__device__ __forceinline__ void store8(__nv_bfloat16 *p, const float v[8]) {
+  uint4 t;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&t);
+#pragma unroll
+  for (int i = 0; i < 4; i++) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+  *reinterpret_cast<uint4 *>(p) = t;
+}
+
+// ---- shared epilogue (4 consecutive output channels of one pixel) ------------------------------
+template <typename T>
+__device__ __forceinline__ void conv_epilogue4(const ConvArgs &a, int b, int y, int x, int n,
+                                               float v[4]) {
+  const BlockGeom g = a.geom[b];
+  const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
+  const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
+  if (a.mode == kEpiForward) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = valid ? fmaxf(v[j] + a.bias[n + j], 0.f) : 0.f;
+  } else {
+    if (a.cact && valid) {
+      const int gy = (g.ey0 >> a.level) + y, gx = (g.ex0 >> a.level) + x;
+      if (gy < a.Hc && gx < a.Wc) {
+        float ca[4], ct[4];
+        load4(reinterpret_cast<const T *>(a.cact) + o, ca);
+        load4(reinterpret_cast<const T *>(a.ctgt) + ((size_t)gy * a.Wc + gx) * a.cout + n, ct);
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] += a.two_lambda * (ca[j] - ct[j]);
+      }
+    }
+    if (a.mask) {
+      float m[4];
+      load4(reinterpret_cast<const T *>(a.mask) + o, m);
+#pragma unroll
+      for (int j = 0; j < 4; j++) v[j] = m[j] > 0.f ? v[j] : 0.f;
+    }
+    if (!valid) v[0] = v[1] = v[2] = v[3] = 0.f;
+  }
+  store4(reinterpret_cast<T *>(a.out) + o, v);
+}
+
+// ---- CUDA-core implicit-GEMM convolution ---------------------------------------------------------
+// CTA tile: 8x8 output pixels x 64 output channels; K slices of 16 channels of one tap.
+// 256 threads, each 4 pixels x 4 channels, FP32 accumulation.
+template <typename T>
+__global__ void __launch_bounds__(256) conv_simt_kernel(ConvArgs a) {
+  __shared__ __align__(16) float As[16][68];
+  __shared__ __align__(16) float Bs[16][68];
+  const int tilesX = (a.Wb + 7) >> 3, tilesY = (a.Hb + 7) >> 3;
+  int t = blockIdx.x;
+  const int tx = t % tilesX;
+  t /= tilesX;
+  const int ty = t % tilesY;
+  const int b = t / tilesY;
+  const int n0 = blockIdx.y * 64;
+  const int tid = threadIdx.x;
+  const int tp = tid & 15, tc = tid >> 4;
+  const int lp = tid >> 2, lc = (tid & 3) * 4;
+  const int py = ty * 8 + (lp >> 3), px = tx * 8 + (lp & 7);
+  const int bn = tid >> 2, bk = (tid & 3) * 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+
+  auto mac = [&]() {
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      float4 av = *reinterpret_cast<const float4 *>(&As[k][tp * 4]);
+      float4 bv = *reinterpret_cast<const float4 *>(&Bs[k][tc * 4]);
+      float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+    }
+  };
+
+  const T *A = reinterpret_cast<const T *>(a.A);
+  const T *Wt = reinterpret_cast<const T *>(a.Wt);
+  for (int tap = 0; tap < a.taps; tap++) {
+    const int y = py + tap / 3 - 1, x = px + tap % 3 - 1;
+    const bool in = y >= 0 && y < a.Hb && x >= 0 && x < a.Wb;
+    const T *arow = A + (((size_t)b * a.Hb + y) * a.Wb + x) * a.cin;
+    const T *brow = Wt + ((size_t)(n0 + bn) * a.taps + tap) * a.cin;
+    for (int c0 = 0; c0 < a.cin; c0 += 16) {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (in) load4(arow + c0 + lc, v);
+#pragma unroll
+      for (int j = 0; j < 4; j++) As[lc + j][lp] = v[j];
+      float w[4];
+      load4(brow + c0 + bk, w);
+#pragma unroll
+      for (int j = 0; j < 4; j++) Bs[bk + j][bn] = w[j];
+      __syncthreads();
+      mac();
+      __syncthreads();
+    }
+  }
+  if (a.k2 > 0) {
+    const T *A2 = reinterpret_cast<const T *>(a.A2);
+    const T *W2 = reinterpret_cast<const T *>(a.W2);
+    const bool in = py < a.Hb && px < a.Wb;
+    const T *arow = A2 + (((size_t)b * a.Hb + py) * a.Wb + px) * a.k2;
+    const T *brow = W2 + (size_t)(n0 + bn) * a.k2;
+    for (int c0 = 0; c0 < a.k2; c0 += 16) {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (in) load4(arow + c0 + lc, v);
+#pragma unroll
+      for (int j = 0; j < 4; j++) As[lc + j][lp] = v[j];
+      float w[4];
+      load4(brow + c0 + bk, w);
+#pragma unroll
+      for (int j = 0; j < 4; j++) Bs[bk + j][bn] = w[j];
+      __syncthreads();
+      mac();
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int p = tp * 4 + i;
+    const int y = ty * 8 + (p >> 3), x = tx * 8 + (p & 7);
+    if (y < a.Hb && x < a.Wb) conv_epilogue4<T>(a, b, y, x, n0 + tc * 4, acc[i]);
+  }
+}
+
+template <typename T>
+void launch_conv_simt(const ConvArgs &a, cudaStream_t s) {
+  dim3 grid(((a.Wb + 7) / 8) * ((a.Hb + 7) / 8) * a.B, a.cout / 64);
+  conv_simt_kernel<T><<<grid, 256, 0, s>>>(a);
+}
+template void launch_conv_simt<float>(const ConvArgs &, cudaStream_t);
+template void launch_conv_simt<__nv_bfloat16>(const ConvArgs &, cudaStream_t);
+
+// ---- conv1_1 forward from the planar image (block extraction fused) ----------------------------
+// out[b][y][x][c] = relu(b1[c] + sum W1[c][ci][ky][kx] * blk(ci, y+ky-1, x+kx-1)), where blk is the
+// block's extended rectangle of x and reads zero outside it (the block is a standalone image).
+template <typename T>
+__global__ void __launch_bounds__(256) conv11_fwd_kernel(const float *__restrict__ img, int H,
+                                                         int W, const float *__restrict__ w11,
+                                                         const float *__restrict__ b11,
+                                                         const BlockGeom *__restrict__ geom,
+                                                         int B, int Hb, int Wb, T *__restrict__ out) {
+  __shared__ float ws[27][64];
+  __shared__ float bs[64];
+  for (int i = threadIdx.x; i < 27 * 64; i += blockDim.x) {
+    const int co = i / 27, k = i % 27;  // k = ci*9 + ky*3 + kx
+    ws[k][co] = w11[i];
+  }
+  if (threadIdx.x < 64) bs[threadIdx.x] = b11[threadIdx.x];
+  __syncthreads();
+  const int cg = threadIdx.x & 3;  // channel group of 16
+  const long long npix = (long long)B * Hb * Wb;
+  for (long long p = (long long)blockIdx.x * 64 + (threadIdx.x >> 2); p < npix;
+       p += (long long)gridDim.x * 64) {
+    const int x = (int)(p % Wb);
+    const int y = (int)((p / Wb) % Hb);
+    const int b = (int)(p / ((long long)Wb * Hb));
+    const BlockGeom g = geom[b];
+    float acc[16];
+    const bool valid = y < g.eh && x < g.ew;
+    if (valid) {
+      float in[27];
+#pragma unroll
+      for (int ci = 0; ci < 3; ci++)
+#pragma unroll
+        for (int ky = 0; ky < 3; ky++)
+#pragma unroll
+          for (int kx = 0; kx < 3; kx++) {
+            const int yy = y + ky - 1, xx = x + kx - 1;
+            const bool ok = yy >= 0 && yy < g.eh && xx >= 0 && xx < g.ew;
+            in[ci * 9 + ky * 3 + kx] =
+                ok ? img[((size_t)ci * H + g.ey0 + yy) * W + g.ex0 + xx] : 0.f;
+          }
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        float s = bs[cg * 16 + j];
+#pragma unroll
+        for (int k = 0; k < 27; k++) s = fmaf(ws[k][cg * 16 + j], in[k], s);
+        acc[j] = fmaxf(s, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; j++) acc[j] = 0.f;
+    }
+    T *o = out + (size_t)p * 64 + cg * 16;
+    store8(o, acc);
+    store8(o + 8, acc + 8);
+  }
+}
+
+template <typename T>
+void launch_conv11_fwd(const float *img, int H, int W, const float *w11, const float *b11,
+                       const BlockGeom *geom, int B, int Hb, int Wb, T *out, cudaStream_t s) {
+  long long npix = (long long)B * Hb * Wb;
+  long long blocks = (npix + 63) / 64;
+  int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+  conv11_fwd_kernel<T><<<grid, 256, 0, s>>>(img, H, W, w11, b11, geom, B, Hb, Wb, out);
+}
+template void launch_conv11_fwd<float>(const float *, int, int, const float *, const float *,
+                                       const BlockGeom *, int, int, int, float *, cudaStream_t);
+template void launch_conv11_fwd<__nv_bfloat16>(const float *, int, int, const float *,
+                                               const float *, const BlockGeom *, int, int, int,
+                                               __nv_bfloat16 *, cudaStream_t);
+
+// ---- conv1_1 input gradient + scatter of the inner part into dE/dx --------------------------------
+// dx[ci](y,x) = sum_{co,ky,kx} W1[co][ci][ky][kx] * g[y-ky+1][x-kx+1][co] for the owned (inner)
+// pixels of each block, written to grad at image coordinates (Algorithm 1, last line).
+template <typename T>
+__global__ void __launch_bounds__(256) conv11_dgrad_scatter_kernel(
+    const T *__restrict__ g, const float *__restrict__ w11, const BlockGeom *__restrict__ geom,
+    const OwnRect *__restrict__ inner, int B, int Hb, int Wb, float *__restrict__ grad, int H,
+    int W) {
+  __shared__ float ws[9][64][3];
+  for (int i = threadIdx.x; i < 64 * 27; i += blockDim.x) {
+    const int co = i / 27, r = i % 27, ci = r / 9, k = r % 9;
+    ws[k][co][ci] = w11[i];
+  }
+  __syncthreads();
+  const int b = blockIdx.y;
+  if (b >= B) return;
+  const OwnRect r = inner[b];
+  const BlockGeom gm = geom[b];
+  const int rw = r.x1 - r.x0, rh = r.y1 - r.y0;
+  const long long n = (long long)rw * rh;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int y = r.y0 + (int)(q / rw), x = r.x0 + (int)(q % rw);
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    for (int ky = 0; ky < 3; ky++)
+      for (int kx = 0; kx < 3; kx++) {
+        const int yy = y - ky + 1, xx = x - kx + 1;
+        if (yy < 0 || yy >= Hb || xx < 0 || xx >= Wb) continue;
+        const T *gp = g + (((size_t)b * Hb + yy) * Wb + xx) * 64;
+        const int k = ky * 3 + kx;
+#pragma unroll 2
+        for (int c8 = 0; c8 < 64; c8 += 8) {
+          float gv[8];
+          load8(gp + c8, gv);
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            d0 = fmaf(ws[k][c8 + j][0], gv[j], d0);
+            d1 = fmaf(ws[k][c8 + j][1], gv[j], d1);
+            d2 = fmaf(ws[k][c8 + j][2], gv[j], d2);
+          }
+        }
+      }
+    const size_t o = (size_t)(gm.ey0 + y) * W + gm.ex0 + x;
+    grad[o] = d0;
+    grad[(size_t)H * W + o] = d1;
+    grad[2 * (size_t)H * W + o] = d2;
+  }
+}
+
+template <typename T>
+void launch_conv11_dgrad_scatter(const T *g, const float *w11, const BlockGeom *geom,
+                                 const OwnRect *inner, int B, int Hb, int Wb, float *grad, int H,
+                                 int W, int max_inner_px, cudaStream_t s) {
+  int gx = (max_inner_px + 255) / 256;
+  if (gx > 1024) gx = 1024;
+  if (gx < 1) gx = 1;
+  dim3 grid(gx, B);
+  conv11_dgrad_scatter_kernel<T><<<grid, 256, 0, s>>>(g, w11, geom, inner, B, Hb, Wb, grad, H, W);
+}
+template void launch_conv11_dgrad_scatter<float>(const float *, const float *, const BlockGeom *,
+                                                 const OwnRect *, int, int, int, float *, int, int,
+                                                 int, cudaStream_t);
+template void launch_conv11_dgrad_scatter<__nv_bfloat16>(const __nv_bfloat16 *, const float *,
+                                                         const BlockGeom *, const OwnRect *, int,
+                                                         int, int, float *, int, int, int,
+                                                         cudaStream_t);
+
+// ---- 2x2 max pool (floor) and its adjoint ----------------------------------------------------------
+// The window's first maximum in row-major order (strict '>') is the argmax, as in the oracle.
+__device__ __forceinline__ int argmax4(float v0, float v1, float v2, float v3) {
+  int k = 0;
+  float m = v0;
+  if (v1 > m) { m = v1; k = 1; }
+  if (v2 > m) { m = v2; k = 2; }
+  if (v3 > m) { k = 3; }
+  return k;
+}
+
+// in: [B][2Hp][2Wp][C] at level l; out: [B][Hp][Wp][C] at level l+1; zero outside valid region
+template <typename T>
+__global__ void pool_kernel(const T *__restrict__ in, T *__restrict__ out, int B, int Hp, int Wp,
+                            int C, const BlockGeom *__restrict__ geom, int level_out) {
+  const int C8 = C / 8;
+  const long long n = (long long)B * Hp * Wp * C8;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C8) * 8;
+    long long p = i / C8;
+    const int x = (int)(p % Wp);
+    const int y = (int)((p / Wp) % Hp);
+    const int b = (int)(p / ((long long)Wp * Hp));
+    const BlockGeom g = geom[b];
+    float o[8];
+    if (y < (g.eh >> level_out) && x < (g.ew >> level_out)) {
+      const int Wi = 2 * Wp;
+      const T *base = in + (((size_t)b * 2 * Hp + 2 * y) * Wi + 2 * x) * C + c;
+      float v0[8], v1[8], v2[8], v3[8];
+      load8(base, v0);
+      load8(base + C, v1);
+      load8(base + (size_t)Wi * C, v2);
+      load8(base + (size_t)Wi * C + C, v3);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int k = argmax4(v0[j], v1[j], v2[j], v3[j]);
+        o[j] = k == 0 ? v0[j] : k == 1 ? v1[j] : k == 2 ? v2[j] : v3[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; j++) o[j] = 0.f;
+    }
+    store8(out + (size_t)p * C + c, o);
+  }
+}
+
+// gp: [B][Hp][Wp][C] gradient w.r.t. the pooled map; act: [B][2Hp][2Wp][C] post-ReLU activation;
+// g:  [B][2Hp][2Wp][C] gradient w.r.t. the pre-activation = routed gp gated by act > 0
+template <typename T>
+__global__ void unpool_kernel(const T *__restrict__ gp, const T *__restrict__ act,
+                              T *__restrict__ g, int B, int Hp, int Wp, int C,
+                              const BlockGeom *__restrict__ geom, int level_out) {
+  const int C8 = C / 8;
+  const long long n = (long long)B * Hp * Wp * C8;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C8) * 8;
+    long long p = i / C8;
+    const int x = (int)(p % Wp);
+    const int y = (int)((p / Wp) % Hp);
+    const int b = (int)(p / ((long long)Wp * Hp));
+    const BlockGeom gm = geom[b];
+    const int Wi = 2 * Wp;
+    const size_t o0 = (((size_t)b * 2 * Hp + 2 * y) * Wi + 2 * x) * C + c;
+    const size_t offs[4] = {o0, o0 + C, o0 + (size_t)Wi * C, o0 + (size_t)Wi * C + C};
+    float r[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) r[k][j] = 0.f;
+    if (y < (gm.eh >> level_out) && x < (gm.ew >> level_out)) {
+      float gv[8], v[4][8];
+      load8(gp + (size_t)p * C + c, gv);
+#pragma unroll
+      for (int k = 0; k < 4; k++) load8(act + offs[k], v[k]);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int k = argmax4(v[0][j], v[1][j], v[2][j], v[3][j]);
+        const float av = k == 0 ? v[0][j] : k == 1 ? v[1][j] : k == 2 ? v[2][j] : v[3][j];
+        const float val = av > 0.f ? gv[j] : 0.f;
+        r[0][j] = k == 0 ? val : 0.f;
+        r[1][j] = k == 1 ? val : 0.f;
+        r[2][j] = k == 2 ? val : 0.f;
+        r[3][j] = k == 3 ? val : 0.f;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) store8(g + offs[k], r[k]);
+  }
+}
+
+static int ew_grid(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
+template <typename T>
+void launch_pool(const T *in, T *out, int B, int Hp, int Wp, int C, const BlockGeom *geom,
+                 int level_out, cudaStream_t s) {
+  pool_kernel<T><<<ew_grid((long long)B * Hp * Wp * C / 8), 256, 0, s>>>(in, out, B, Hp, Wp, C,
+                                                                          geom, level_out);
+}
+template <typename T>
+void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C,
+                   const BlockGeom *geom, int level_out, cudaStream_t s) {
+  unpool_kernel<T><<<ew_grid((long long)B * Hp * Wp * C / 8), 256, 0, s>>>(gp, act, g, B, Hp, Wp,
+                                                                            C, geom, level_out);
+}
+template void launch_pool<float>(const float *, float *, int, int, int, int, const BlockGeom *,
+                                 int, cudaStream_t);
+template void launch_pool<__nv_bfloat16>(const __nv_bfloat16 *, __nv_bfloat16 *, int, int, int,
+                                         int, const BlockGeom *, int, cudaStream_t);
+template void launch_unpool<float>(const float *, const float *, float *, int, int, int, int,
+                                   const BlockGeom *, int, cudaStream_t);
+template void launch_unpool<__nv_bfloat16>(const __nv_bfloat16 *, const __nv_bfloat16 *,
+                                           __nv_bfloat16 *, int, int, int, int, const BlockGeom *,
+                                           int, cudaStream_t);
+
+// ---- Gram partial sums over owned pixels (CUDA cores) --------------------------------------------
+// chunk c covers pixels [p0, p1) of block b's owned rectangle (row-major inside the rectangle);
+// CTA (c, pair) accumulates the 64x64 block (I, J), I <= J, of sum_p V_p V_p^T in FP32 and writes
+// it to part[(c * npairs + pair) * 4096 + i * 64 + j].
+template <typename T>
+__global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__ V, int Hb, int Wb,
+                                                           int C, const OwnRect *__restrict__ own,
+                                                           const GramChunk *__restrict__ chunks,
+                                                           float *__restrict__ part) {
+  __shared__ __align__(16) float Ai[32][68];
+  __shared__ __align__(16) float Aj[32][68];
+  const int nb = C / 64;
+  const int npairs = nb * (nb + 1) / 2;
+  int pair = blockIdx.y, I = 0;
+  while (pair >= nb - I) { pair -= nb - I; I++; }
+  const int J = I + pair;
+  const GramChunk ch = chunks[blockIdx.x];
+  const OwnRect r = own[ch.b];
+  const int rw = r.x1 - r.x0;
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const int lp = tid >> 3, lc = (tid & 7) * 8;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+  for (int q0 = ch.p0; q0 < ch.p1; q0 += 32) {
+    const int q = q0 + lp;
+    float vi[8], vj[8];
+    if (q < ch.p1) {
+      const int y = r.y0 + q / rw, x = r.x0 + q % rw;
+      const T *row = V + (((size_t)ch.b * Hb + y) * Wb + x) * C;
+      load8(row + I * 64 + lc, vi);
+      load8(row + J * 64 + lc, vj);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; k++) vi[k] = vj[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      Ai[lp][lc + k] = vi[k];
+      Aj[lp][lc + k] = vj[k];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int p = 0; p < 32; p++) {
+      float4 a4 = *reinterpret_cast<const float4 *>(&Ai[p][ti * 4]);
+      float4 b4 = *reinterpret_cast<const float4 *>(&Aj[p][tj * 4]);
+      float ar[4] = {a4.x, a4.y, a4.z, a4.w}, br[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float *o = part + ((size_t)blockIdx.x * npairs + blockIdx.y) * 4096;
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+    *reinterpret_cast<float4 *>(o + (ti * 4 + i) * 64 + tj * 4) =
+        make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+}
+
+// Gacc[C][C] += sum over chunks (fixed order, FP64) of the partial blocks; mirrored for I != J
+__global__ void gram_reduce_kernel(const float *__restrict__ part, int nchunks, int C,
+                                   double *__restrict__ Gacc) {
+  const int nb = C / 64;
+  const int npairs = nb * (nb + 1) / 2;
+  const long long n = (long long)npairs * 4096;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    int pair = (int)(e / 4096), I = 0;
+    const int k = (int)(e % 4096);
+    while (pair >= nb - I) { pair -= nb - I; I++; }
+    const int J = I + pair;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += (double)part[((size_t)c * npairs) * 4096 + e];
+    const int i = I * 64 + k / 64, j = J * 64 + k % 64;
+    Gacc[(size_t)i * C + j] += s;
+    if (I != J) Gacc[(size_t)j * C + i] += s;
+  }
+}
+
+template <typename T>
+void launch_gram_partial(const T *V, int Hb, int Wb, int C, const OwnRect *own,
+                         const GramChunk *chunks, int nchunks, float *part, cudaStream_t s) {
+  const int nb = C / 64;
+  dim3 grid(nchunks, nb * (nb + 1) / 2);
+  gram_partial_kernel<T><<<grid, 256, 0, s>>>(V, Hb, Wb, C, own, chunks, part);
+}
+template void launch_gram_partial<float>(const float *, int, int, int, const OwnRect *,
+                                         const GramChunk *, int, float *, cudaStream_t);
+template void launch_gram_partial<__nv_bfloat16>(const __nv_bfloat16 *, int, int, int,
+                                                 const OwnRect *, const GramChunk *, int, float *,
+                                                 cudaStream_t);
+void launch_gram_reduce(const float *part, int nchunks, int C, double *Gacc, cudaStream_t s) {
+  const int nb = C / 64;
+  long long n = (long long)nb * (nb + 1) / 2 * 4096;
+  gram_reduce_kernel<<<ew_grid(n), 256, 0, s>>>(part, nchunks, C, Gacc);
+}
+
+// ---- style finalisation: G = Gacc / np, E_L = w ||G - Ghat||^2, R = (4 w / np)(G - Ghat) -------------
+// One CTA of 1024 threads per style layer; deterministic reduction.
+__global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs a) {
+  __shared__ double red[1024];
+  const StyleLayerArgs L = a.L[blockIdx.x];
+  const long long n = (long long)L.C * L.C;
+  const double inv = 1.0 / L.np, rs = 4.0 * L.w / L.np;
+  double s = 0.0;
+  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+    const double G = L.Gacc[e] * inv;
+    const double d = G - L.Ghat[e];
+    L.Gout[e] = G;
+    s += d * d;
+    if (a.r_is_bf16)
+      reinterpret_cast<__nv_bfloat16 *>(L.R)[e] = __float2bfloat16_rn((float)(rs * d));
+    else
+      reinterpret_cast<float *>(L.R)[e] = (float)(rs * d);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 512; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.Eparts[blockIdx.x] = L.w * red[0];
+}
+
+void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s) {
+  style_finalize_kernel<<<kNStyle, 1024, 0, s>>>(a);
+}
+
+// ---- content loss over owned pixels: partial[c] = sum (V - Vu)^2 (FP64) ----------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) content_partial_kernel(
+    const T *__restrict__ V, int Hb, int Wb, const T *__restrict__ Vu, int Hc, int Wc,
+    const BlockGeom *__restrict__ geom, const OwnRect *__restrict__ own,
+    const GramChunk *__restrict__ chunks, double *__restrict__ partial) {
+  __shared__ double red[256];
+  const GramChunk ch = chunks[blockIdx.x];
+  const OwnRect r = own[ch.b];
+  const BlockGeom g = geom[ch.b];
+  const int rw = r.x1 - r.x0;
+  const int oy = g.ey0 >> kContentLevel, ox = g.ex0 >> kContentLevel;
+  double s = 0.0;
+  // 64 threads per pixel row of 512 channels (8 each)
+  for (int q = ch.p0 + (threadIdx.x >> 6); q < ch.p1; q += 4) {
+    const int y = r.y0 + q / rw, x = r.x0 + q % rw;
+    const int c = (threadIdx.x & 63) * 8;
+    float a[8], t[8];
+    load8(V + (((size_t)ch.b * Hb + y) * Wb + x) * 512 + c, a);
+    load8(Vu + ((size_t)(oy + y) * Wc + ox + x) * 512 + c, t);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const double d = (double)a[j] - (double)t[j];
+      s += d * d;
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// acc += lambda * sum_c partial[c] in fixed order (single thread: the chunk count is small)
+__global__ void content_reduce_kernel(const double *__restrict__ partial, int n, double lambda,
+                                      double *__restrict__ acc) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += partial[i];
+    *acc += lambda * s;
+  }
+}
+
+template <typename T>
+void launch_content_loss(const T *V, int Hb, int Wb, const T *Vu, int Hc, int Wc,
+                         const BlockGeom *geom, const OwnRect *own, const GramChunk *chunks,
+                         int nchunks, double *partial, double lambda, double *acc,
+                         cudaStream_t s) {
+  if (nchunks > 0) {
+    content_partial_kernel<T><<<nchunks, 256, 0, s>>>(V, Hb, Wb, Vu, Hc, Wc, geom, own, chunks,
+                                                      partial);
+    content_reduce_kernel<<<1, 32, 0, s>>>(partial, nchunks, lambda, acc);
+  }
+}
+template void launch_content_loss<float>(const float *, int, int, const float *, int, int,
+                                         const BlockGeom *, const OwnRect *, const GramChunk *,
+                                         int, double *, double, double *, cudaStream_t);
+template void launch_content_loss<__nv_bfloat16>(const __nv_bfloat16 *, int, int,
+                                                 const __nv_bfloat16 *, int, int,
+                                                 const BlockGeom *, const OwnRect *,
+                                                 const GramChunk *, int, double *, double,
+                                                 double *, cudaStream_t);
+
+// ---- content target crop: owned ReLU4_2 features of each block into the global map ------------------
+template <typename T>
+__global__ void crop_content_kernel(const T *__restrict__ V, int B, int Hb, int Wb,
+                                    const BlockGeom *__restrict__ geom,
+                                    const OwnRect *__restrict__ own, T *__restrict__ Vu, int Hc,
+                                    int Wc) {
+  const int b = blockIdx.y;
+  const OwnRect r = own[b];
+  const BlockGeom g = geom[b];
+  const int rw = r.x1 - r.x0;
+  const long long n = (long long)(r.y1 - r.y0) * rw * 64;
+  const int oy = g.ey0 >> kContentLevel, ox = g.ex0 >> kContentLevel;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % 64) * 8;
+    const long long q = i / 64;
+    const int y = r.y0 + (int)(q / rw), x = r.x0 + (int)(q % rw);
+    float v[8];
+    load8(V + (((size_t)b * Hb + y) * Wb + x) * 512 + c, v);
+    store8(Vu + ((size_t)(oy + y) * Wc + ox + x) * 512 + c, v);
+  }
+  (void)B;
+  (void)Hc;
+}
+
+template <typename T>
+void launch_crop_content(const T *V, int B, int Hb, int Wb, const BlockGeom *geom,
+                         const OwnRect *own, T *Vu, int Hc, int Wc, int max_own_px,
+                         cudaStream_t s) {
+  int gx = (int)(((long long)max_own_px * 64 + 255) / 256);
+  if (gx > 2048) gx = 2048;
+  if (gx < 1) gx = 1;
+  crop_content_kernel<T><<<dim3(gx, B), 256, 0, s>>>(V, B, Hb, Wb, geom, own, Vu, Hc, Wc);
+}
+template void launch_crop_content<float>(const float *, int, int, int, const BlockGeom *,
+                                         const OwnRect *, float *, int, int, int, cudaStream_t);
+template void launch_crop_content<__nv_bfloat16>(const __nv_bfloat16 *, int, int, int,
+                                                 const BlockGeom *, const OwnRect *,
+                                                 __nv_bfloat16 *, int, int, int, cudaStream_t);
+
+// ---- misc ---------------------------------------------------------------------------------------
+__global__ void check_finite_kernel(const float *__restrict__ x, long long n,
+                                    unsigned *__restrict__ err) {
+  bool bad = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonfinite);
+}
+void launch_check_finite(const float *x, long long n, unsigned *err, cudaStream_t s) {
+  check_finite_kernel<<<ew_grid(n), 256, 0, s>>>(x, n, err);
+}
+
+// loss = sum of the five style parts + content part, in fixed order
+__global__ void finish_loss_kernel(const double *__restrict__ parts, double *__restrict__ loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < kNStyle + 1; i++) s += parts[i];
+    if (loss) *loss = s;
+  }
+}
+void launch_finish_loss(const double *parts, double *loss, cudaStream_t s) {
+  finish_loss_kernel<<<1, 32, 0, s>>>(parts, loss);
+}
+
+}  // namespace nst

@@ -1,0 +1,138 @@
+// nst_api_opt.cu -- C ABI of the optimiser step (L-BFGS, Section 3.1 / Section 5.1) and of the
+// multiscale initialisation (Algorithm 2).
+#include <cstring>
+#include <string>
+
+#include "../../include/nst.h"
+#include "nst_kernels.h"
+#include "nst_lbfgs_dev.h"
+
+using namespace nst;
+
+struct nst_lbfgs {
+  long long n = 0;
+  int m = 0;
+  long long iters = 0;
+  float *S = nullptr, *Y = nullptr;  // [m+1][n] history slots
+  float *g_prev = nullptr, *q = nullptr;
+  double *rho = nullptr, *alpha = nullptr, *partials = nullptr;
+  LbfgsCtl *ctl = nullptr;
+};
+
+namespace {
+constexpr double kCurvEps = 1e-10;
+}
+
+extern "C" {
+
+nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m) {
+  if (!out || n <= 0 || m < 1 || m > kMaxHistory) return NST_ERR_INVALID_ARG;
+  *out = nullptr;
+  nst_lbfgs *st = new nst_lbfgs();
+  st->n = n;
+  st->m = m;
+  const size_t slots = (size_t)(m + 1);
+  bool ok = cudaMalloc(&st->S, slots * n * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&st->Y, slots * n * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&st->g_prev, n * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&st->q, n * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&st->rho, slots * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&st->alpha, (size_t)m * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&st->partials, dot_partials_count() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&st->ctl, sizeof(LbfgsCtl)) == cudaSuccess;
+  if (!ok) {
+    nst_lbfgs_destroy(st);
+    return NST_ERR_OOM;
+  }
+  cudaMemset(st->S, 0, slots * n * sizeof(float));
+  cudaMemset(st->Y, 0, slots * n * sizeof(float));
+  cudaMemset(st->rho, 0, slots * sizeof(double));
+  cudaMemset(st->alpha, 0, (size_t)m * sizeof(double));
+  LbfgsCtl c;
+  std::memset(&c, 0, sizeof(c));
+  c.gamma = 1.0;
+  c.one = 1.0;
+  c.t_first = 1.0;
+  c.count = 0;
+  c.spare = 0;
+  for (int i = 0; i < kMaxHistory; i++) c.order[i] = -1;
+  cudaMemcpy(st->ctl, &c, sizeof(c), cudaMemcpyHostToDevice);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    nst_lbfgs_destroy(st);
+    return NST_ERR_CUDA;
+  }
+  *out = st;
+  return NST_OK;
+}
+
+nst_status nst_lbfgs_destroy(nst_lbfgs *st) {
+  if (!st) return NST_OK;
+  cudaDeviceSynchronize();
+  cudaFree(st->S); cudaFree(st->Y); cudaFree(st->g_prev); cudaFree(st->q);
+  cudaFree(st->rho); cudaFree(st->alpha); cudaFree(st->partials); cudaFree(st->ctl);
+  delete st;
+  return NST_OK;
+}
+
+nst_status nst_lbfgs_step(nst_lbfgs *st, float *x, const float *g, void *stream) {
+  if (!st || !x || !g) return NST_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = st->n;
+  const int m = st->m;
+  LbfgsCtl *c = st->ctl;
+  const VecRef spareS{st->S, &c->spare, n}, spareY{st->Y, &c->spare, n};
+  if (st->iters > 0) {
+    // candidate pair: s (stored last step) and y = g - g_prev, both in the spare slot
+    launch_sub_ref(spareY, g, st->g_prev, n, s);
+    launch_dot_ref(spareY, spareS, n, st->partials, &c->ys, nullptr, nullptr, 0, s);
+    launch_dot_ref(spareY, spareY, n, st->partials, &c->yy, nullptr, nullptr, 0, s);
+    launch_lbfgs_accept(c, st->rho, m, kCurvEps, s);
+  } else {
+    launch_dot_ref(VecRef{g, nullptr, 0}, VecRef{nullptr, nullptr, 0}, n, st->partials,
+                   &c->t_first, nullptr, nullptr, 1, s);
+  }
+  // two-loop recursion: q = g; newest -> oldest: alpha_i = rho_i s_i^T q, q -= alpha_i y_i
+  if (cudaMemcpyAsync(st->q, g, n * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return NST_ERR_CUDA;
+  for (int i = 0; i < m; i++) {
+    const VecRef Si{st->S, &c->order[i], n}, Yi{st->Y, &c->order[i], n};
+    launch_dot_ref(Si, VecRef{st->q, nullptr, 0}, n, st->partials, &st->alpha[i], st->rho,
+                   &c->order[i], 0, s);
+    launch_axpy_ref(st->q, Yi, n, &st->alpha[i], nullptr, -1.f, s);
+  }
+  // r = gamma q; oldest -> newest: beta = rho_i y_i^T r, r += (alpha_i - beta) s_i
+  launch_scale_dev(st->q, st->q, n, &c->gamma, s);
+  for (int i = m - 1; i >= 0; i--) {
+    const VecRef Si{st->S, &c->order[i], n}, Yi{st->Y, &c->order[i], n};
+    double *beta = &c->beta;
+    launch_dot_ref(Yi, VecRef{st->q, nullptr, 0}, n, st->partials, beta, st->rho, &c->order[i],
+                   0, s);
+    launch_axpy_ref(st->q, Si, n, &st->alpha[i], beta, 1.f, s);
+  }
+  // d = -r; x += t d; the step goes to the spare slot for the next pair
+  launch_lbfgs_finish_ref(x, spareS, st->g_prev, st->q, g, n,
+                          st->iters == 0 ? &c->t_first : &c->one, s);
+  if (cudaGetLastError() != cudaSuccess) return NST_ERR_CUDA;
+  st->iters++;
+  return NST_OK;
+}
+
+nst_status nst_lbfgs_info(nst_lbfgs *st, int *pairs, long long *iters, void *stream) {
+  if (!st) return NST_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return NST_ERR_CUDA;
+  LbfgsCtl c;
+  if (cudaMemcpy(&c, st->ctl, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return NST_ERR_CUDA;
+  if (pairs) *pairs = c.count;
+  if (iters) *iters = st->iters;
+  return NST_OK;
+}
+
+nst_status nst_upsample_init(const float *xs, int h, int w, float *x, int H, int W,
+                             void *stream) {
+  if (!xs || !x || h < 1 || w < 1 || H < 1 || W < 1) return NST_ERR_INVALID_ARG;
+  launch_bicubic(xs, 3, h, w, x, H, W, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? NST_OK : NST_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// nst_kernels.h -- host-side declarations of the library's kernel launchers.
+#pragma once
+#include "nst_internal.cuh"
+
+namespace nst {
+
+// a run of owned pixels [p0, p1) of block b (row-major inside its owned rectangle)
+struct GramChunk {
+  int b, p0, p1, pad;
+};
+
+struct StyleLayerArgs {
+  const double *Gacc;  // sum over owned pixels of V V^T (FP64)
+  const double *Ghat;  // G^L(v)
+  double *Gout;        // G^L(x) = Gacc / np
+  void *R;             // (4 w / np)(G - Ghat), FP32 or BF16
+  int C;
+  double np;
+  double w;
+};
+struct StyleFinalizeArgs {
+  StyleLayerArgs L[kNStyle];
+  double *Eparts;  // [5]
+  int r_is_bf16;
+};
+
+// k_simt.cu
+template <typename T> void launch_conv_simt(const ConvArgs &a, cudaStream_t s);
+template <typename T>
+void launch_conv11_fwd(const float *img, int H, int W, const float *w11, const float *b11,
+                       const BlockGeom *geom, int B, int Hb, int Wb, T *out, cudaStream_t s);
+template <typename T>
+void launch_conv11_dgrad_scatter(const T *g, const float *w11, const BlockGeom *geom,
+                                 const OwnRect *inner, int B, int Hb, int Wb, float *grad, int H,
+                                 int W, int max_inner_px, cudaStream_t s);
+template <typename T>
+void launch_pool(const T *in, T *out, int B, int Hp, int Wp, int C, const BlockGeom *geom,
+                 int level_out, cudaStream_t s);
+template <typename T>
+void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C,
+                   const BlockGeom *geom, int level_out, cudaStream_t s);
+template <typename T>
+void launch_gram_partial(const T *V, int Hb, int Wb, int C, const OwnRect *own,
+                         const GramChunk *chunks, int nchunks, float *part, cudaStream_t s);
+void launch_gram_reduce(const float *part, int nchunks, int C, double *Gacc, cudaStream_t s);
+void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s);
+template <typename T>
+void launch_content_loss(const T *V, int Hb, int Wb, const T *Vu, int Hc, int Wc,
+                         const BlockGeom *geom, const OwnRect *own, const GramChunk *chunks,
+                         int nchunks, double *partial, double lambda, double *acc, cudaStream_t s);
+template <typename T>
+void launch_crop_content(const T *V, int B, int Hb, int Wb, const BlockGeom *geom,
+                         const OwnRect *own, T *Vu, int Hc, int Wc, int max_own_px,
+                         cudaStream_t s);
+void launch_check_finite(const float *x, long long n, unsigned *err, cudaStream_t s);
+void launch_finish_loss(const double *parts, double *loss, cudaStream_t s);
+
+// k_tc.cu: tcgen05 / TMEM / TMA implicit-GEMM convolution (BF16 in, FP32 accumulate)
+// Returns cudaSuccess or the error of tensor-map encoding / launch.
+cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s);
+bool tc_available();
+
+// k_lbfgs.cu (L-BFGS launchers are declared in nst_lbfgs_dev.h)
+void launch_bicubic(const float *x, int C, int h, int w, float *out, int H, int W,
+                    cudaStream_t s);
+
+}  // namespace nst

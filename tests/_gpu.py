@@ -1,0 +1,57 @@
+"""Helpers for the GPU parity tests: run libnst and the FP64 oracle on the same seeded problem."""
+import functools
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2212_13459_gb300 import native, synth
+from tests._common import LAMBDA_C, W_STYLE, rel_l2  # noqa: F401
+
+# tolerances of the two forms of the path (relative L2 error of dE/dx and |dE|/|E|)
+TOL_FP32 = 1e-5
+TOL_BF16 = 2e-2
+
+
+@functools.lru_cache(maxsize=None)
+def seeded(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
+    params = synth.vgg19_params(seed, bias_std=bias_std)
+    u = synth.content_image(H, W, seed)
+    v = synth.noise_style(Hv or H, Wv or W, seed)
+    rng = np.random.default_rng(seed + 100)
+    x = np.clip(u + noise * rng.standard_normal(u.shape), 0, 1).astype(np.float32)
+    return params, u, v, x
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
+    params, u, v, x = seeded(H, W, seed, Hv, Wv, noise, bias_std)
+    P = oracle.pack_params(params)
+    ct = oracle.content_target(P, u)
+    Gv = oracle.style_grams(P, v)
+    E, g, parts, Gx = oracle.loss_grad(P, x, ct, Gv, W_STYLE, LAMBDA_C)
+    return E, g, parts, Gx, Gv
+
+
+def run_gpu(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, x=None, **cfg):
+    params, u, v, x0 = seeded(H, W, seed, Hv, Wv, noise, bias_std)
+    x = x0 if x is None else x
+    cfg.setdefault("w_style", W_STYLE)
+    cfg.setdefault("lambda_c", LAMBDA_C)
+    ctx = native.Context(synth.flat_params(params), **cfg)
+    dev = torch.device("cuda:0")
+    ut = torch.from_numpy(u).to(dev)
+    vt = torch.from_numpy(v).to(dev)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    ctx.style_targets(vt)
+    ctx.content_targets(ut)
+    grad = torch.empty_like(xt)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    ctx.loss_grad(xt, grad, loss)
+    torch.cuda.synchronize()
+    st = ctx.sync_status()
+    parts, grams = ctx.stats()
+    out = dict(E=float(loss.item()), g=grad.cpu().numpy().astype(np.float64), parts=parts,
+               grams=grams, style_grams=ctx.style_grams(), status=st)
+    ctx.close()
+    return out

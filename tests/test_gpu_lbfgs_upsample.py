@@ -1,0 +1,56 @@
+"""GPU parity of the L-BFGS step (nst_lbfgs_step) and of the bicubic initialisation
+(nst_upsample_init) against the FP64 oracles."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bicubic, lbfgs
+from paper_2212_13459_gb300 import native
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,m,steps", [(1000, 5, 25), (4099, 10, 12), (257, 3, 40)])
+def test_lbfgs_iterates_match_oracle(n, m, steps):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((64, n)) / np.sqrt(n)
+    d = rng.uniform(0.5, 2.0, size=n)
+    b = rng.standard_normal(n)
+    grad = lambda z: d * z + A.T @ (A @ z) - b        # strictly convex quadratic
+    x_ref = np.zeros(n)
+    opt = lbfgs.LBFGS(n, m)
+    x_gpu = torch.zeros(n, dtype=torch.float32, device="cuda")
+    st = native.LBFGS(n, m)
+    for k in range(steps):
+        # both sides get the gradient at their own iterate (FP32 on the device)
+        g_ref = grad(x_ref)
+        opt.step(x_ref, g_ref)
+        g_dev = torch.from_numpy(grad(x_gpu.cpu().numpy().astype(np.float64)).astype(np.float32))
+        st.step(x_gpu, g_dev.cuda())
+    xg = x_gpu.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
+    pairs, iters = st.info()
+    assert iters == steps and pairs == min(m, len(opt.S))
+
+
+def test_lbfgs_first_step():
+    g = torch.tensor([3.0, -1.0, 0.5, 0.0], device="cuda")
+    x = torch.zeros(4, device="cuda")
+    st = native.LBFGS(4, 10)
+    st.step(x, g)
+    assert np.allclose(x.cpu().numpy(), -g.cpu().numpy() / 4.5, rtol=1e-6)
+
+
+@pytest.mark.parametrize("h,w,H,W", [(13, 17, 26, 34), (1512, 2016, 3024, 4032), (7, 9, 15, 20)])
+def test_upsample_matches_oracle(h, w, H, W):
+    rng = np.random.default_rng(h * w)
+    xs = rng.uniform(0, 1, size=(3, h, w)).astype(np.float32)
+    out = torch.empty((3, H, W), device="cuda")
+    native.upsample_init(torch.from_numpy(xs).cuda(), out)
+    ref = bicubic.upsample(xs.astype(np.float64), H, W)
+    got = out.cpu().numpy()
+    if H * W > 10 ** 6:   # full size: sampled rows
+        rows = rng.integers(0, H, size=64)
+        assert np.abs(got[:, rows] - ref[:, rows]).max() <= 1e-5
+    else:
+        assert np.abs(got - ref).max() <= 1e-5

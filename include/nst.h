@@ -147,6 +147,21 @@ nst_status nst_lbfgs_info(nst_lbfgs *st, int *pairs, long long *iters, void *str
 nst_status nst_upsample_init(const float *x_small_dev, int h, int w, float *x_dev, int H, int W,
                              void *stream);
 
+/* ---- single-layer convolution (unit-test entry of the convolution engines) -------------------
+ * One 3x3 convolution layer of the trunk on NHWC tensors, as used inside nst_loss_grad:
+ *   acc[b][y][x][n] = sum_{ky,kx,c} in[b][y+ky-1][x+kx-1][c] * w[n][ky*3+kx][c]      (taps = 9)
+ *                   + sum_c in2[b][y][x][c] * w2[n][c]                               (k2 > 0)
+ * with zero padding outside H x W. mode 0 (forward): out = relu(acc + bias[n]), and 0 outside the
+ * valid region geom_dev[b] = {ey0, ex0, eh, ew} (eh/ew at this layer's resolution, level 0).
+ * mode 1 (backward): out = acc * (mask > 0) (mask may be NULL: no gate), 0 outside the valid
+ * region. dtype: NST_PREC_FP32 (float tensors) or NST_PREC_BF16 (bfloat16 tensors); engine:
+ * NST_CONV_SIMT or NST_CONV_TC (BF16 only). taps is 9 or 0; cin, cout, k2 multiples of 64 (TC) or
+ * 16 (SIMT). All pointers are device pointers owned by the caller. */
+nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int cout, int taps,
+                       const void *in_dev, const void *w_dev, int k2, const void *in2_dev,
+                       const void *w2_dev, const float *bias_dev, int mode, const void *mask_dev,
+                       const int *geom_dev, void *out_dev, void *stream);
+
 /* Library version string. */
 const char *nst_version(void);
 

@@ -87,7 +87,9 @@ __global__ void axpy_kernel(float *__restrict__ y, VecRef rx, long long n,
   const float *x = resolve(rx);
   if (!x) return;
   const float c = sign * (float)(*c1 - (c2 ? *c2 : 0.0));
-  const long long n4 = n / 4;
+  // the float4 path needs both vectors 16-byte aligned; otherwise everything goes scalar
+  const bool vec = (((uintptr_t)y | (uintptr_t)x) & 15) == 0;
+  const long long n4 = vec ? n / 4 : 0;
   float4 *y4 = reinterpret_cast<float4 *>(y);
   const float4 *x4 = reinterpret_cast<const float4 *>(x);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;

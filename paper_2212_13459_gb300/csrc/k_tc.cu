@@ -1,6 +1,494 @@
-// k_tc.cu -- placeholder: the tcgen05 engine is not built yet.
+// k_tc.cu -- tensor-core implicit-GEMM 3x3 convolution for sm_103a: tcgen05.mma (BF16 inputs,
+// FP32 accumulator in tensor memory), operands staged in shared memory by TMA, warp-specialised
+// and persistent. It runs every convolution of the VGG-19 trunk except conv1_1 (Cin = 3):
+//   forward:  out = relu(W * in + b), zero outside each block's valid region (Section 3.1);
+//   backward: out = (W^T * g [+ V R_L] [+ 2 lambda (V - V_u)]) gated by the ReLU mask, i.e. the
+//             input gradient of a convolution with the style-loss feature gradient V R_L
+//             (Table 1 row 2, R_L = 4 w_L (G - G_ref) / n_p) fused as extra K, and the content
+//             gradient (Table 1 row 1) fused in the epilogue (Algorithm 1, Step 2).
+//
+// GEMM view: M = output pixels of a TH x TW patch (TH * TW = 128), N = output channels (tile BN),
+// K = 9 taps x Cin (+ K2). The A tile of one (tap, 64-channel) K-block is one 4-D TMA box of the
+// NHWC activation at the tap's offset: out-of-range coordinates read as zero, which is exactly
+// the convolution's zero padding. Both operands use the 128-byte swizzled K-major layout.
+//
+// Roles (192 threads): warp 0 issues TMA, warp 1 owns TMEM and issues tcgen05.mma, warps 2..5
+// drain the accumulator (tcgen05.ld), apply the epilogue and store BF16. Two TMEM accumulators
+// let the epilogue of one tile overlap the main loop of the next. Every mbarrier wait is bounded:
+// on timeout the kernel latches kErrTimeout in the status word and returns.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "nst_internal.cuh"
 #include "nst_kernels.h"
+
 namespace nst {
-bool tc_available() { return false; }
-cudaError_t launch_conv_tc(const ConvArgs &, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int kThreads = 192;
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kBK = 64;                           // channels per K-block (128 bytes of BF16)
+
+struct TcGeom {
+  int TH, TW;           // output patch per M tile
+  int tiles_x, tiles_y; // patches per block image
+  int n_tiles;          // N tiles (cout / BN)
+  int total;            // M tiles * N tiles
+  int kb_main;          // taps * cin / 64
+  int kb2;              // k2 / 64
+  int cin_blocks;       // cin / 64
+};
+
+// ---- PTX wrappers ----------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false if the CTA aborted or the wait ran out (status latched)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      if (err) atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading-dimension offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride-dimension offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n.
+__host__ __device__ constexpr uint32_t make_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+// ---- epilogue for 32 consecutive channels of one pixel ------------------------------------------
+__device__ __forceinline__ void ld_bf16x8(const __nv_bfloat16 *p, float *v) {
+  uint4 t = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&t);
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    float2 f = __bfloat1622float2(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+__device__ __forceinline__ void st_bf16x8(__nv_bfloat16 *p, const float *v) {
+  uint4 t;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&t);
+#pragma unroll
+  for (int i = 0; i < 4; i++) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+  *reinterpret_cast<uint4 *>(p) = t;
+}
+
+__device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g, int b, int y,
+                                           int x, int n, float *v) {
+  const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
+  const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
+  if (a.mode == kEpiForward) {
+#pragma unroll
+    for (int j = 0; j < 32; j++) v[j] = valid ? fmaxf(v[j] + __ldg(a.bias + n + j), 0.f) : 0.f;
+  } else {
+    if (!valid) {
+#pragma unroll
+      for (int j = 0; j < 32; j++) v[j] = 0.f;
+    } else {
+      if (a.cact) {
+        const int gy = (g.ey0 >> a.level) + y, gx = (g.ex0 >> a.level) + x;
+        if (gy < a.Hc && gx < a.Wc) {
+          const __nv_bfloat16 *ca = reinterpret_cast<const __nv_bfloat16 *>(a.cact) + o;
+          const __nv_bfloat16 *ct = reinterpret_cast<const __nv_bfloat16 *>(a.ctgt) +
+                                    ((size_t)gy * a.Wc + gx) * a.cout + n;
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            float c8[8], t8[8];
+            ld_bf16x8(ca + 8 * q, c8);
+            ld_bf16x8(ct + 8 * q, t8);
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[8 * q + j] += a.two_lambda * (c8[j] - t8[j]);
+          }
+        }
+      }
+      if (a.mask) {
+        const __nv_bfloat16 *mk = reinterpret_cast<const __nv_bfloat16 *>(a.mask) + o;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          float m8[8];
+          ld_bf16x8(mk + 8 * q, m8);
+#pragma unroll
+          for (int j = 0; j < 8; j++) v[8 * q + j] = m8[j] > 0.f ? v[8 * q + j] : 0.f;
+        }
+      }
+    }
+  }
+  __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out) + o;
+#pragma unroll
+  for (int q = 0; q < 4; q++) st_bf16x8(out + 8 * q, v + 8 * q);
+}
+
+// ---- the kernel -------------------------------------------------------------------------------------
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmA2,
+                   const __grid_constant__ CUtensorMap tmB2, const ConvArgs a, const TcGeom tg) {
+  constexpr uint32_t A_BYTES = 128 * kBK * 2;
+  constexpr uint32_t B_BYTES = BN * kBK * 2;
+  constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t IDESC = make_idesc(BN);
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(smem_u32(&tfull_bar[i]), 1);
+      mbar_init(smem_u32(&tempty_bar[i]), 128);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+  const int kb_total = tg.kb_main + tg.kb2;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
+        const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
+        const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
+        const int b = mt / (tg.tiles_x * tg.tiles_y);
+        const int x0 = tx * tg.TW, y0 = ty * tg.TH, n0 = nt * BN;
+        for (int kb = 0; kb < kb_total; kb++) {
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          if (kb < tg.kb_main) {
+            const int tap = kb / tg.cin_blocks, cb = kb % tg.cin_blocks;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            tma_load_4d(sa, &tmA, fb, cb * kBK, x0 + dx, y0 + dy, b);
+            tma_load_2d(sb, &tmB, fb, tap * a.cin + cb * kBK, n0);
+          } else {
+            const int cb = kb - tg.kb_main;
+            tma_load_4d(sa, &tmA2, fb, cb * kBK, x0, y0, b);
+            tma_load_2d(sb, &tmB2, fb, cb * kBK, n0);
+          }
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x, it++) {
+        const int acc = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < kb_total; kb++) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+          const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; k++)
+            mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
+                     (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty_bar[stage]));
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (ok) mma_commit(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int q = warp & 3;           // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;    // M row = pixel of the patch
+    int it = 0;
+    for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
+      const int acc = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      if (!mbar_wait(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      tc_fence_after();
+      const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
+      const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
+      const int b = mt / (tg.tiles_x * tg.tiles_y);
+      const int y = ty * tg.TH + row / tg.TW, x = tx * tg.TW + row % tg.TW;
+      const bool inb = y < a.Hb && x < a.Wb;
+      const BlockGeom g = a.geom[b];
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c, v);
+        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty_bar[acc]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+// ---- host side -------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn g_encode = nullptr;
+int g_num_sms = 0;
+bool g_tc_ok = false;
+std::once_flag g_once;
+
+void init_once() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return;
+  g_num_sms = prop.multiProcessorCount;
+  if (prop.major != 10) return;  // tcgen05 needs a Blackwell data-center part
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return;
+  g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  g_tc_ok = true;
+}
+
+// NHWC BF16 activation [B][H][W][C] as a 4-D tensor map with a (64, TW, TH, 1) box
+cudaError_t encode_act(CUtensorMap *m, const void *ptr, int B, int H, int W, int C, int TH,
+                       int TW) {
+  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)TW, (cuuint32_t)TH, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// weights [N][K] (K contiguous) as a 2-D tensor map with a (64, BN) box
+cudaError_t encode_wt(CUtensorMap *m, const void *ptr, int N, int K, int BN) {
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)BN};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_bn(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
+                      const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
+                      cudaStream_t s) {
+  constexpr size_t smem = (size_t)STAGES * (128 * kBK * 2 + BN * kBK * 2) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int grid = std::min(tg.total, g_num_sms);
+  conv_tc_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
+  return cudaGetLastError();
+}
+
+// output patch shape with the least padding over an H x W map (TH * TW = 128)
+void pick_patch(int H, int W, int &TH, int &TW) {
+  static const int cand[5][2] = {{1, 128}, {2, 64}, {4, 32}, {8, 16}, {16, 8}};
+  long long best = -1;
+  for (auto &c : cand) {
+    const long long area = (long long)((H + c[0] - 1) / c[0]) * c[0] * ((W + c[1] - 1) / c[1]) *
+                           c[1];
+    if (best < 0 || area < best) { best = area; TH = c[0]; TW = c[1]; }
+  }
+}
+
+}  // namespace
+
+bool tc_available() {
+  std::call_once(g_once, init_once);
+  return g_tc_ok;
+}
+
+cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
+  if (!tc_available()) return cudaErrorNotSupported;
+  if ((a.taps != 0 && a.taps != 9) || a.cout % 64 || (a.taps && a.cin % 64) || a.k2 % 64 ||
+      (a.taps == 0 && a.k2 == 0))
+    return cudaErrorInvalidValue;
+  const int BN = a.cout >= 256 ? 256 : a.cout;
+  TcGeom tg;
+  pick_patch(a.Hb, a.Wb, tg.TH, tg.TW);
+  tg.tiles_x = (a.Wb + tg.TW - 1) / tg.TW;
+  tg.tiles_y = (a.Hb + tg.TH - 1) / tg.TH;
+  tg.n_tiles = a.cout / BN;
+  tg.total = a.B * tg.tiles_x * tg.tiles_y * tg.n_tiles;
+  tg.cin_blocks = a.taps ? a.cin / kBK : 0;
+  tg.kb_main = a.taps * tg.cin_blocks;
+  tg.kb2 = a.k2 / kBK;
+  CUtensorMap mA, mB, mA2, mB2;
+  cudaError_t e;
+  if (a.taps) {
+    if ((e = encode_act(&mA, a.A, a.B, a.Hb, a.Wb, a.cin, tg.TH, tg.TW)) != cudaSuccess) return e;
+    if ((e = encode_wt(&mB, a.Wt, a.cout, a.taps * a.cin, BN)) != cudaSuccess) return e;
+  }
+  if (a.k2) {
+    if ((e = encode_act(&mA2, a.A2, a.B, a.Hb, a.Wb, a.k2, tg.TH, tg.TW)) != cudaSuccess) return e;
+    if ((e = encode_wt(&mB2, a.W2, a.cout, a.k2, BN)) != cudaSuccess) return e;
+  }
+  if (!a.taps) { mA = mA2; mB = mB2; }
+  if (!a.k2) { mA2 = mA; mB2 = mB; }
+  switch (BN) {
+    case 64: return launch_bn<64, 8>(mA, mB, mA2, mB2, a, tg, s);
+    case 128: return launch_bn<128, 6>(mA, mB, mA2, mB2, a, tg, s);
+    case 256: return launch_bn<256, 4>(mA, mB, mA2, mB2, a, tg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace nst

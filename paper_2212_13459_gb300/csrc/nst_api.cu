@@ -900,4 +900,44 @@ nst_status nst_sync_status(nst_ctx *ctx, void *stream) {
   return NST_OK;
 }
 
+nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int cout, int taps,
+                       const void *in, const void *w, int k2, const void *in2, const void *w2,
+                       const float *bias, int mode, const void *mask, const int *geom, void *out,
+                       void *stream) {
+  nst_ctx *ctx = nullptr;
+  if ((dtype != NST_PREC_FP32 && dtype != NST_PREC_BF16) ||
+      (engine != NST_CONV_SIMT && engine != NST_CONV_TC) || (taps != 0 && taps != 9) || B < 1 ||
+      H < 1 || W < 1 || cout < 1 || cout % 64 || k2 < 0 || (taps && (!in || !w || cin < 16)) ||
+      (k2 && (!in2 || !w2)) || (!taps && !k2) || !geom || !out || (mode != 0 && mode != 1) ||
+      (mode == 0 && !bias))
+    return fail(nullptr, NST_ERR_INVALID_ARG, "bad convolution arguments");
+  if (engine == NST_CONV_TC && (dtype != NST_PREC_BF16 || (taps && cin % 64) || k2 % 64))
+    return fail(nullptr, NST_ERR_INVALID_ARG, "tensor-core engine: BF16, channels % 64");
+  if (engine == NST_CONV_SIMT && ((taps && cin % 16) || k2 % 16))
+    return fail(nullptr, NST_ERR_INVALID_ARG, "CUDA-core engine: channels % 16");
+  ConvArgs a{};
+  a.B = B; a.Hb = H; a.Wb = W;
+  a.cin = taps ? cin : 0; a.cout = cout; a.taps = taps;
+  a.k2 = k2; a.A = in; a.Wt = w; a.A2 = in2; a.W2 = w2;
+  a.out = out;
+  a.mode = mode;
+  a.bias = bias;
+  a.mask = mask;
+  a.geom = reinterpret_cast<const BlockGeom *>(geom);
+  a.level = 0;
+  a.err = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (engine == NST_CONV_TC)
+    e = launch_conv_tc(a, s);
+  else if (dtype == NST_PREC_BF16)
+    launch_conv_simt<__nv_bfloat16>(a, s);
+  else
+    launch_conv_simt<float>(a, s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "nst_conv3x3");
+  return NST_OK;
+}
+
 }  // extern "C"
+

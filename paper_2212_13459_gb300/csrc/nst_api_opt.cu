@@ -11,6 +11,7 @@ using namespace nst;
 
 struct nst_lbfgs {
   long long n = 0;
+  long long stride = 0;              // slot stride: n rounded up to 64 floats (256-byte slots)
   int m = 0;
   long long iters = 0;
   float *S = nullptr, *Y = nullptr;  // [m+1][n] history slots
@@ -31,9 +32,10 @@ nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m) {
   nst_lbfgs *st = new nst_lbfgs();
   st->n = n;
   st->m = m;
+  st->stride = (n + 63) / 64 * 64;
   const size_t slots = (size_t)(m + 1);
-  bool ok = cudaMalloc(&st->S, slots * n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&st->Y, slots * n * sizeof(float)) == cudaSuccess &&
+  bool ok = cudaMalloc(&st->S, slots * st->stride * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&st->Y, slots * st->stride * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&st->g_prev, n * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&st->q, n * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&st->rho, slots * sizeof(double)) == cudaSuccess &&
@@ -44,8 +46,8 @@ nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m) {
     nst_lbfgs_destroy(st);
     return NST_ERR_OOM;
   }
-  cudaMemset(st->S, 0, slots * n * sizeof(float));
-  cudaMemset(st->Y, 0, slots * n * sizeof(float));
+  cudaMemset(st->S, 0, slots * st->stride * sizeof(float));
+  cudaMemset(st->Y, 0, slots * st->stride * sizeof(float));
   cudaMemset(st->rho, 0, slots * sizeof(double));
   cudaMemset(st->alpha, 0, (size_t)m * sizeof(double));
   LbfgsCtl c;
@@ -80,7 +82,8 @@ nst_status nst_lbfgs_step(nst_lbfgs *st, float *x, const float *g, void *stream)
   const long long n = st->n;
   const int m = st->m;
   LbfgsCtl *c = st->ctl;
-  const VecRef spareS{st->S, &c->spare, n}, spareY{st->Y, &c->spare, n};
+  const long long ss = st->stride;
+  const VecRef spareS{st->S, &c->spare, ss}, spareY{st->Y, &c->spare, ss};
   if (st->iters > 0) {
     // candidate pair: s (stored last step) and y = g - g_prev, both in the spare slot
     launch_sub_ref(spareY, g, st->g_prev, n, s);
@@ -95,7 +98,7 @@ nst_status nst_lbfgs_step(nst_lbfgs *st, float *x, const float *g, void *stream)
   if (cudaMemcpyAsync(st->q, g, n * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return NST_ERR_CUDA;
   for (int i = 0; i < m; i++) {
-    const VecRef Si{st->S, &c->order[i], n}, Yi{st->Y, &c->order[i], n};
+    const VecRef Si{st->S, &c->order[i], ss}, Yi{st->Y, &c->order[i], ss};
     launch_dot_ref(Si, VecRef{st->q, nullptr, 0}, n, st->partials, &st->alpha[i], st->rho,
                    &c->order[i], 0, s);
     launch_axpy_ref(st->q, Yi, n, &st->alpha[i], nullptr, -1.f, s);
@@ -103,7 +106,7 @@ nst_status nst_lbfgs_step(nst_lbfgs *st, float *x, const float *g, void *stream)
   // r = gamma q; oldest -> newest: beta = rho_i y_i^T r, r += (alpha_i - beta) s_i
   launch_scale_dev(st->q, st->q, n, &c->gamma, s);
   for (int i = m - 1; i >= 0; i--) {
-    const VecRef Si{st->S, &c->order[i], n}, Yi{st->Y, &c->order[i], n};
+    const VecRef Si{st->S, &c->order[i], ss}, Yi{st->Y, &c->order[i], ss};
     double *beta = &c->beta;
     launch_dot_ref(Yi, VecRef{st->q, nullptr, 0}, n, st->partials, beta, st->rho, &c->order[i],
                    0, s);

@@ -76,6 +76,8 @@ def lib():
                                     ctypes.POINTER(ctypes.c_longlong), vp], ip),
                 "nst_upsample_init": ([fp, ip, ip, fp, ip, ip, vp], ip),
                 "nst_version": ([], ctypes.c_char_p),
+                "nst_conv3x3": ([ip, ip, ip, ip, ip, ip, ip, ip, vp, vp, ip, vp, vp, vp, ip, vp,
+                                 vp, vp, vp], ip),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -242,3 +244,15 @@ class LBFGS:
 def upsample_init(x_small, out, stream=None):
     _check(lib().nst_upsample_init(_ptr(x_small), x_small.shape[1], x_small.shape[2], _ptr(out),
                                    out.shape[1], out.shape[2], _stream(stream)))
+
+
+def conv3x3(dtype, engine, inp, w, out, bias=None, mode=0, mask=None, in2=None, w2=None,
+            geom=None, taps=9, stream=None):
+    """One convolution layer (unit-test entry). inp [B,H,W,cin], w [cout,taps,cin],
+    in2 [B,H,W,k2], w2 [cout,k2], out [B,H,W,cout], geom int32 [B,4] (device)."""
+    B, H, W, cout = out.shape
+    cin = inp.shape[3] if inp is not None else 0
+    k2 = in2.shape[3] if in2 is not None else 0
+    _check(lib().nst_conv3x3(dtype, engine, B, H, W, cin, cout, taps, _ptr(inp), _ptr(w), k2,
+                             _ptr(in2), _ptr(w2), _ptr(bias), mode, _ptr(mask), _ptr(geom),
+                             _ptr(out), _stream(stream)))

@@ -1,0 +1,146 @@
+"""The tensor-core (tcgen05/TMEM/TMA) convolution engine.
+
+Unit level: one layer through nst_conv3x3 against PyTorch's own FP32 conv2d of the same
+BF16-rounded inputs (forward with bias/ReLU/valid-region zeroing, backward gating by a mask, the
+fused style-gradient K extension V R, and that extension alone), for the channel counts of the
+VGG-19 trunk and ragged spatial sizes. Path level: the full Algorithm 1 evaluation with the
+tensor-core engine against the FP64 oracle (BF16 tolerance 2e-2).
+"""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+from paper_2212_13459_gb300 import native
+from tests._gpu import TOL_BF16, oracle_result, rel_l2, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _ref(inp, w, in2, w2, bias, mode, mask, geom):
+    """FP32 reference on the given tensors (NHWC)."""
+    B, H, W, _ = (inp if inp is not None else in2).shape
+    cout = (w if w is not None else w2).shape[0]
+    acc = torch.zeros(B, H, W, cout, device="cuda")
+    if inp is not None:
+        cin = inp.shape[3]
+        wt = w.float().view(cout, 3, 3, cin).permute(0, 3, 1, 2).contiguous()
+        acc += F.conv2d(inp.float().permute(0, 3, 1, 2), wt, padding=1).permute(0, 2, 3, 1)
+    if in2 is not None:
+        acc += torch.einsum("bhwk,nk->bhwn", in2.float(), w2.float())
+    valid = torch.zeros(B, H, W, 1, device="cuda", dtype=torch.bool)
+    for b in range(B):
+        valid[b, :geom[b, 2], :geom[b, 3]] = True
+    if mode == 0:
+        out = torch.relu(acc + bias.view(1, 1, 1, -1))
+    else:
+        out = acc if mask is None else acc * (mask.float() > 0)
+    return out * valid
+
+
+CASES = [  # B, H, W, cin, cout, k2, taps, mode
+    (2, 13, 37, 64, 64, 0, 9, 0),
+    (1, 9, 130, 128, 256, 0, 9, 0),
+    (3, 5, 6, 256, 512, 0, 9, 0),
+    (2, 17, 24, 512, 512, 0, 9, 0),
+    (2, 11, 19, 64, 128, 128, 9, 1),
+    (1, 33, 21, 512, 256, 256, 9, 1),
+    (2, 7, 9, 0, 512, 512, 0, 1),
+    (1, 64, 64, 64, 64, 64, 9, 1),
+]
+
+
+@pytest.mark.parametrize("engine", [native.CONV_TC, native.CONV_SIMT])
+@pytest.mark.parametrize("case", CASES)
+def test_single_layer_bf16(engine, case):
+    B, H, W, cin, cout, k2, taps, mode = case
+    g = torch.Generator(device="cuda").manual_seed(B * 1000 + H * 10 + cout)
+    bf = torch.bfloat16
+    inp = torch.rand(B, H, W, cin, device="cuda", generator=g).to(bf) if taps else None
+    w = (torch.randn(cout, 9, cin, device="cuda", generator=g) / (3 * cin ** 0.5)).to(bf) \
+        if taps else None
+    in2 = torch.rand(B, H, W, k2, device="cuda", generator=g).to(bf) if k2 else None
+    w2 = (torch.randn(cout, k2, device="cuda", generator=g) / k2 ** 0.5).to(bf) if k2 else None
+    bias = torch.randn(cout, device="cuda", generator=g) * 0.1
+    mask = (torch.randn(B, H, W, cout, device="cuda", generator=g) > 0).to(bf) if mode else None
+    geom = torch.tensor([[0, 0, H - (b % 2) * 2, W - (b % 2) * 3] for b in range(B)],
+                        dtype=torch.int32, device="cuda")
+    out = torch.full((B, H, W, cout), 7.0, device="cuda", dtype=bf)
+    native.conv3x3(native.PREC_BF16, engine, inp, w, out, bias=bias, mode=mode, mask=mask,
+                   in2=in2, w2=w2, geom=geom, taps=taps)
+    torch.cuda.synchronize()
+    ref = _ref(inp, w, in2, w2, bias, mode, mask, geom.cpu())
+    err = (out.float() - ref).norm() / ref.norm()
+    assert err.item() <= 1e-2, err.item()
+    # everything outside the valid region is exactly zero
+    for b in range(B):
+        assert torch.count_nonzero(out[b, geom[b, 2]:]).item() == 0
+        assert torch.count_nonzero(out[b, :, geom[b, 3]:]).item() == 0
+
+
+def test_single_layer_fp32_simt():
+    B, H, W, cin, cout = 2, 10, 23, 64, 128
+    g = torch.Generator(device="cuda").manual_seed(5)
+    inp = torch.rand(B, H, W, cin, device="cuda", generator=g)
+    w = torch.randn(cout, 9, cin, device="cuda", generator=g) / (3 * cin ** 0.5)
+    bias = torch.randn(cout, device="cuda", generator=g) * 0.1
+    geom = torch.tensor([[0, 0, H, W]] * B, dtype=torch.int32, device="cuda")
+    out = torch.empty(B, H, W, cout, device="cuda")
+    native.conv3x3(native.PREC_FP32, native.CONV_SIMT, inp, w, out, bias=bias, geom=geom)
+    torch.backends.cudnn.allow_tf32 = False
+    ref = _ref(inp, w, None, None, bias, 0, None, geom.cpu())
+    assert ((out - ref).norm() / ref.norm()).item() <= 1e-5
+
+
+def _cmp(res, ref, tol):
+    E, g, parts, Gx, Gv = ref
+    assert res["status"] == 0
+    for s in range(5):
+        assert rel_l2(res["style_grams"][s], Gv[s]) <= tol, s
+        assert rel_l2(res["grams"][s], Gx[s]) <= tol, s
+    assert abs(res["E"] - E) <= tol * abs(E)
+    assert rel_l2(res["g"], g) <= tol, rel_l2(res["g"], g)
+
+
+TC = dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC)
+
+
+def test_path_tc_config1():
+    _cmp(run_gpu(64, 64, 0, tiles_h=2, tiles_w=2, **TC), oracle_result(64, 64, 0), TOL_BF16)
+
+
+def test_path_tc_untiled_128():
+    _cmp(run_gpu(128, 128, 1, **TC), oracle_result(128, 128, 1), TOL_BF16)
+
+
+def test_path_tc_ragged_bias():
+    _cmp(run_gpu(100, 76, 2, Hv=90, Wv=111, bias_std=0.01, tiles_h=2, tiles_w=3, **TC),
+         oracle_result(100, 76, 2, Hv=90, Wv=111, bias_std=0.01), TOL_BF16)
+
+
+def test_path_tc_margins_cut_blocks():
+    _cmp(run_gpu(96, 480, 3, tiles_h=1, tiles_w=3, **TC), oracle_result(96, 480, 3), TOL_BF16)
+
+
+def test_path_tc_matches_simt_bf16():
+    """Same BF16 storage, different MMA engine: the two agree far inside the BF16 tolerance."""
+    a = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, **TC)
+    b = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, precision=native.PREC_BF16,
+                conv_engine=native.CONV_SIMT)
+    assert rel_l2(a["g"], b["g"]) <= 1e-2
+    assert abs(a["E"] - b["E"]) <= 1e-3 * abs(b["E"])
+
+
+def test_path_tc_identity_exact_zero():
+    from tests._gpu import seeded
+    from paper_2212_13459_gb300 import synth
+    params, u, v, x = seeded(192, 160, 4)
+    ctx = native.Context(synth.flat_params(params), tiles_h=2, tiles_w=2, **TC)
+    ut = torch.from_numpy(u).cuda()
+    ctx.style_targets(ut)
+    ctx.content_targets(ut)
+    g = torch.full_like(ut, 7.0)
+    loss = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+    ctx.loss_grad(ut, g, loss)
+    torch.cuda.synchronize()
+    assert loss.item() == 0.0 and torch.count_nonzero(g).item() == 0

@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput of the localized style-transfer loss + image-gradient evaluation (Algorithm 1).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload scale3|scale4|scale1] [--precision bf16|fp32]
+
+A step is one evaluation of E(x) and dE/dx through the C ABI (nst_loss_grad): both passes over
+all blocks with margins, every kernel of the path. The default workload is the 3024 x 4032 scale
+of the multiscale driver with 8 x 8 blocks: content / x0 = bicubic x2 (nst_upsample_init) of a
+synthetic 1512 x 2016 previous-scale result, style = 2113 x 2660 synthetic stroke texture.
+Inputs are resident in HBM when the timed region starts; they are larger than L2 (the
+activations of one pass are tens of GB), so no flush is needed between steps.
+
+Prints ONE JSON line on rank 0. With --gpus N > 1 (launched by torchrun) each rank runs an
+independent replica of the workload on its own GPU ("replicas": the method itself is one-GPU);
+value = all ranks' pixels / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the plain definition) on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "megapixels/s of loss+image-gradient evals at 3024×4032; % BF16 TC peak"
+# algorithmic FLOPs per image pixel of one evaluation: 2 VGG-19 forwards to ReLU5_1, one
+# input-gradient pass, Gram accumulation and style-gradient products (2 * 34,816)
+FLOP_PER_PX = 2 * 722304 + 722304 + 2 * 34816
+
+WORKLOADS = {
+    "scale3": dict(H=3024, W=4032, Hv=2113, Wv=2660, seed=3, tiles=8, small=(1512, 2016)),
+    "scale4": dict(H=6048, W=8064, Hv=4226, Wv=5319, seed=4, tiles=16, small=(3024, 4032)),
+    "scale1": dict(H=756, W=1008, Hv=1057, Wv=1330, seed=2, tiles=1, small=None),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return dict(hbm=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]),
+                    bf16_sus=float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                    source="measured")
+    except Exception:
+        return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "nst_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(seed, budget_s=12.0, side=256):
+    """The FP64 oracle as it stands, untiled evaluations of a side x side sample of the same
+    generators; returns (Mpx/s, seconds, evals, threads)."""
+    import oracle
+    from paper_2212_13459_gb300 import synth
+    params = synth.vgg19_params(seed)
+    P = oracle.pack_params(params)
+    u = synth.content_image(side, side, seed)
+    v = synth.stroke_style(side, side, seed, n_strokes=200)
+    ct = oracle.content_target(P, u)
+    Gv = oracle.style_grams(P, v)
+    x = np.clip(0.5 * u + 0.5 * v, 0, 1)
+    ws = np.full(5, 0.2)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.loss_grad(P, x, ct, Gv, ws, 1e-3)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s or n >= 20:
+            break
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return side * side * n / dt / 1e6, dt, n, threads
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    import oracle
+    from paper_2212_13459_gb300 import synth
+    side = 256
+    params = synth.vgg19_params(wl["seed"])
+    P = oracle.pack_params(params)
+    u = synth.content_image(side, side, wl["seed"])
+    v = synth.stroke_style(side, side, wl["seed"], n_strokes=200)
+    ct = oracle.content_target(P, u)
+    Gv = oracle.style_grams(P, v)
+    x = np.clip(0.5 * u + 0.5 * v, 0, 1)
+    ws = np.full(5, 0.2)
+    for _ in range(args.warmup):
+        oracle.loss_grad(P, x, ct, Gv, ws, 1e-3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.loss_grad(P, x, ct, Gv, ws, 1e-3)
+    dt = time.perf_counter() - t0
+    val = side * side * args.steps / dt / 1e6
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = ("untiled FP64 oracle evaluation of a %dx%d sample of the workload's generators "
+              "(seed %d) per step; per-pixel cost of the definition" % (side, side, wl["seed"]))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpx/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "Mpx/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Mpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2212_13459_gb300 import native, synth
+    from paper_2212_13459_gb300 import build as nbuild
+    nbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = WORKLOADS[args.workload]
+    H, W, seed, k = wl["H"], wl["W"], wl["seed"], args.tiles or wl["tiles"]
+    prec = native.PREC_BF16 if args.precision == "bf16" else native.PREC_FP32
+    params = synth.vgg19_params(seed)
+    flat = synth.flat_params(params)
+    v = torch.from_numpy(synth.stroke_style(wl["Hv"], wl["Wv"], seed)).to(dev)
+    u = torch.from_numpy(synth.content_image(H, W, seed)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.empty((3, H, W), device=dev)
+    t_up = None
+    if wl["small"]:
+        xs = torch.from_numpy(synth.scale2_result(wl["small"][0], wl["small"][1], seed)).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        native.upsample_init(xs, x)          # warm-up
+        e0.record(stream)
+        native.upsample_init(xs, x)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_up = e0.elapsed_time(e1)
+    else:
+        x.copy_(torch.clamp(0.5 * u + 0.25, 0, 1))
+    ctx = native.Context(flat, tiles_h=k, tiles_w=k, precision=prec,
+                         margin1=args.margin1, margin2=args.margin2)
+    ctx.style_targets(v)
+    ctx.content_targets(u)
+    grad = torch.empty_like(x)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        ctx.loss_grad(x, grad, loss)
+    torch.cuda.synchronize(dev)
+    if ctx.sync_status() != 0:
+        raise RuntimeError("device status after warm-up: %s" % native.lib().nst_last_error(ctx.h))
+    # ---- timed region: K evaluations, CUDA events on the launching stream ----
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ctx.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.loss_grad(x, grad, loss)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    tm = ctx.timing()
+    ctx.set_timing(False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    value = world * H * W * args.steps / (ms / 1e3) / 1e6
+    E = float(loss.item())
+    status = ctx.sync_status()
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region) ----
+    xh = torch.empty((3, H, W), dtype=torch.float32, pin_memory=True)
+    xh.copy_(x.cpu())
+    gh = torch.empty_like(xh).pin_memory()
+    xh_np, gh_np = xh.numpy(), gh.numpy()
+    ctx.loss_grad_host(xh_np, gh_np)
+    e2e_steps = max(2, min(args.steps, 5))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.loss_grad_host(xh_np, gh_np)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * H * W * e2e_steps / e2e_s / 1e6, "unit": "Mpx/s",
+           "h2d_bytes_per_step": 3 * H * W * 4, "d2h_bytes_per_step": 3 * H * W * 4 + 8,
+           "steps": e2e_steps}
+
+    # ---- optimiser step (driver, per iteration) ----
+    opt = native.LBFGS(3 * H * W, 10)
+    xl = x.clone()
+    for _ in range(12):
+        opt.step(xl, grad)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        opt.step(xl, grad)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    lbfgs_ms = e0.elapsed_time(e1) / 5
+    opt.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    conv_tflops = tm["conv_flops"] / (tm["conv_ms"] / 1e3) / 1e12 if tm["conv_ms"] > 0 else None
+    peak_conv = peaks["bf16_sus"] if prec == native.PREC_BF16 else None
+    roofline = None
+    if prec == native.PREC_BF16 and conv_tflops:
+        roofline = {"bound": "tensor", "kernel": "conv_tc_kernel (tcgen05 implicit-GEMM conv)",
+                    "achieved": conv_tflops, "peak": peak_conv, "unit": "TFLOP/s",
+                    "frac": conv_tflops / peak_conv, "traffic": read_traffic(),
+                    "peak_source": "%s bf16_tflops_sustained" % peaks["source"],
+                    "launches_per_step": tm["conv_launches"] / args.steps,
+                    "ms_per_step": tm["conv_ms"] / args.steps,
+                    "flops_per_launch": tm["conv_flops"] / max(1, tm["conv_launches"])}
+    alg_tflops = FLOP_PER_PX * H * W / (ms_step / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "%s: content %dx%d (x0 = bicubic x2 of a synthetic %s previous-"
+                               "scale result), style %dx%d stroke texture, seed %d, %dx%d blocks, "
+                               "margins %d/%d" % (args.workload, H, W, wl["small"], wl["Hv"],
+                                                  wl["Wv"], seed, k, k, args.margin1,
+                                                  args.margin2),
+                   "H": H, "W": W, "blocks": "%dx%d" % (k, k), "engine": "tcgen05" if
+                   prec == native.PREC_BF16 else "fp32-simt",
+                   "l2": "inputs larger than L2 (activations of one pass >> 129 MB); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pct_bf16_peak_algorithmic": 100.0 * alg_tflops / peaks["bf16_sus"],
+        "algorithmic_tflops": alg_tflops,
+        "roofline": roofline,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": tm["launches"],
+        "loss": E, "device_status": status,
+        "kernel_ms_per_step": {"conv": tm["conv_ms"] / args.steps,
+                               "gram": tm["gram_ms"] / args.steps,
+                               "other": tm["other_ms"] / args.steps},
+        "driver": {"lbfgs_step_ms": lbfgs_ms, "upsample_init_ms": t_up},
+    }
+    ctx.close()
+    if args.compare_fp32 and prec == native.PREC_BF16:
+        out["fp32_form"] = fp32_compare(flat, u, v, x, grad, k, args, dev)
+    if not args.no_cpu_baseline:
+        rate, dt, n, threads = cpu_oracle_rate(seed)
+        out["cpu_baseline"] = {"value": rate, "unit": "Mpx/s", "cores": threads, "kind": "oracle",
+                               "sample": "%d untiled FP64 oracle evaluations of a 256x256 sample "
+                                         "of the workload's generators, %.1f s" % (n, dt)}
+    if dist:
+        dist.destroy_process_group()
+    print(json.dumps(out), flush=True)
+
+
+def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev):
+    """The plain FP32 form (CUDA-core convolutions, FP32 storage) on the same GPU: time and the
+    BF16 gradient's relative error against it."""
+    import torch
+    from paper_2212_13459_gb300 import native
+    ctx = native.Context(flat, tiles_h=k, tiles_w=k, precision=native.PREC_FP32,
+                         margin1=args.margin1, margin2=args.margin2)
+    ctx.style_targets(v)
+    ctx.content_targets(u)
+    g32 = torch.empty_like(x)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    ctx.loss_grad(x, g32, loss)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.loss_grad(x, g32, loss)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    rel = float((grad_bf16 - g32).norm() / g32.norm())
+    ctx.close()
+    H, W = x.shape[1], x.shape[2]
+    return {"ms_per_step": ms, "value": H * W / ms / 1e3, "unit": "Mpx/s",
+            "bf16_speedup": None, "bf16_grad_rel_err_vs_fp32": rel, "loss_fp32": loss.item()}
+
+
+def read_traffic():
+    """DRAM bytes per launch of the convolution kernel from the committed ncu summary, if its
+    recorded source hash matches the current kernel source; else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2212_13459_gb300", "csrc", "k_tc.cu")
+    summ = os.path.join(ROOT, "profiles", "conv_tc_traffic.txt")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = dict(line.strip().split("=", 1) for line in open(summ) if "=" in line)
+        if kv.get("k_tc_sha256_16") == h:
+            return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale3", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--tiles", type=int, default=0)
+    ap.add_argument("--margin1", type=int, default=80)
+    ap.add_argument("--margin2", type=int, default=160)
+    ap.add_argument("--compare-fp32", dest="compare_fp32", action="store_true", default=True)
+    ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

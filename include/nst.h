@@ -110,11 +110,14 @@ nst_status nst_get_stats(nst_ctx *ctx, double *parts_host, double *grams_host, v
 /* The stored style Gram matrices G^L(v) (same layout as grams_host above). Synchronizes. */
 nst_status nst_get_style_grams(nst_ctx *ctx, double *grams_host, void *stream);
 
-/* Per-kernel-class device time of the last nst_loss_grad when timing is enabled
- * (nst_set_timing), in milliseconds, and algorithmic FLOP counts of the tensor-core / SIMT
- * convolutions it ran: out[0] = conv ms, out[1] = conv FLOPs, out[2] = gram ms, out[3] = other
- * ms, out[4] = conv launches, out[5] = total kernel launches. Synchronizes. */
+/* Per-kernel-class device time accumulated since the last nst_set_timing() call (CUDA events
+ * around every launch while timing is enabled), in milliseconds, and the FLOPs the convolution
+ * launches executed (2 * pixels * Cout * (9 Cin + K2) per launch, padding included):
+ * out[0] = convolution ms, out[1] = convolution FLOPs, out[2] = Gram ms, out[3] = other ms,
+ * out[4] = convolution launches, out[5] = all kernel launches (counted with timing on or off).
+ * Synchronizes `stream`. */
 nst_status nst_get_timing(nst_ctx *ctx, double *out6, void *stream);
+/* Enable or disable per-launch event timing; either way the counters restart from zero. */
 nst_status nst_set_timing(nst_ctx *ctx, int enable);
 
 /* Synchronize `stream` and return (then clear) the latched device status. */

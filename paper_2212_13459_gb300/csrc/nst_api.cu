@@ -758,7 +758,6 @@ nst_status nst_style_targets(nst_ctx *ctx, const float *v, int Hv, int Wv, void 
   nst_status st = check_img(ctx, v, Hv, Wv);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  reset_counters(ctx);
   CK(cudaMemsetAsync(ctx->d_gacc, 0, sizeof(double) * kGramTotal, s));
   st = ctx->bf16 ? stats_pass<__nv_bfloat16>(ctx, v, Hv, Wv, kPassStyleStats, s)
                  : stats_pass<float>(ctx, v, Hv, Wv, kPassStyleStats, s);
@@ -788,7 +787,6 @@ nst_status nst_content_targets(nst_ctx *ctx, const float *u, int H, int W, void 
   nst_status st = check_img(ctx, u, H, W);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  reset_counters(ctx);
   const int Hc = H / 8, Wc = W / 8;
   const size_t need = (size_t)Hc * Wc * 512 * ctx->esz;
   if (need > ctx->ctgt_cap) {
@@ -817,7 +815,6 @@ nst_status nst_loss_grad(nst_ctx *ctx, const float *x, int H, int W, float *grad
     return fail(ctx, NST_ERR_STATE, "style and content targets must be set first");
   if (H != ctx->H || W != ctx->W)
     return fail(ctx, NST_ERR_SHAPE, "image size differs from the content target's");
-  reset_counters(ctx);
   cudaStream_t s = (cudaStream_t)stream;
   return ctx->bf16 ? loss_grad_impl<__nv_bfloat16>(ctx, x, grad, loss, s)
                    : loss_grad_impl<float>(ctx, x, grad, loss, s);
@@ -866,7 +863,12 @@ nst_status nst_get_style_grams(nst_ctx *ctx, double *grams, void *stream) {
 
 nst_status nst_set_timing(nst_ctx *ctx, int enable) {
   if (!ctx) return fail(nullptr, NST_ERR_INVALID_ARG, "null context");
+  if (ctx->timing) {
+    cudaError_t e = cudaDeviceSynchronize();  // pending events must complete before reuse
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "nst_set_timing");
+  }
   ctx->timing = enable != 0;
+  reset_counters(ctx);
   return NST_OK;
 }
 

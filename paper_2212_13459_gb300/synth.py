@@ -70,7 +70,7 @@ def content_image(H: int, W: int, seed: int = 0) -> np.ndarray:
         x0 = int(rng.integers(0, max(1, W - w)))
         col = rng.uniform(0, 1, size=3)
         img[:, y0:y0 + h, x0:x0 + w] = col[:, None, None]
-    return np.clip(img, 0, 1).astype(np.float32)
+    return np.ascontiguousarray(np.clip(img, 0, 1), dtype=np.float32)
 
 
 def _value_noise(H, W, rng, octaves=5, persistence=0.5, base=4):
@@ -109,7 +109,7 @@ def noise_style(H: int, W: int, seed: int = 0) -> np.ndarray:
     i0 = np.clip(np.floor(n).astype(int), 0, len(pal) - 2)
     t = (n - i0)[..., None]
     img = pal[i0] * (1 - t) + pal[i0 + 1] * t
-    return np.clip(img.transpose(2, 0, 1), 0, 1).astype(np.float32)
+    return np.ascontiguousarray(np.clip(img.transpose(2, 0, 1), 0, 1), dtype=np.float32)
 
 
 def stroke_style(H: int, W: int, seed: int = 0, n_strokes: int = 2000) -> np.ndarray:
@@ -158,11 +158,11 @@ def stroke_style(H: int, W: int, seed: int = 0, n_strokes: int = 2000) -> np.nda
     yy = np.arange(H)[:, None]
     xx = np.arange(W)[None, :]
     img += (0.05 * np.sin(2 * np.pi * xx / 8) * np.sin(2 * np.pi * yy / 8))[..., None]
-    return np.clip(img.transpose(2, 0, 1), 0, 1).astype(np.float32)
+    return np.ascontiguousarray(np.clip(img.transpose(2, 0, 1), 0, 1), dtype=np.float32)
 
 
 def scale2_result(H: int, W: int, seed: int = 0) -> np.ndarray:
     """A stand-in for the output of the previous scale: content generator with a stroke overlay."""
     base = content_image(H, W, seed)
     strokes = stroke_style(H, W, seed + 7, n_strokes=max(200, (H * W) // 4000))
-    return np.clip(0.6 * base + 0.4 * strokes, 0, 1).astype(np.float32)
+    return np.ascontiguousarray(np.clip(0.6 * base + 0.4 * strokes, 0, 1), dtype=np.float32)

@@ -69,6 +69,7 @@ def lib():
                                           dp, dp]
             L.orc_table1_mse.argtypes = [dp, dp, ctypes.c_long, ctypes.c_double, dp, dp]
             L.orc_plan_1d.argtypes = [ctypes.c_int, ctypes.c_int, ip]
+            L.orc_set_storage.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -83,6 +84,25 @@ def _p(a):
 def _check(rc):
     if rc != 0:
         raise RuntimeError("oracle error %d" % rc)
+
+
+STORAGE = {"f64": 0, "f32": 1, "bf16": 2}
+
+
+class storage:
+    """Context manager: evaluate the oracle with values rounded where the evaluated form stores
+    them (\"f32\" or \"bf16\"; \"f64\" = the plain definition). See nst_oracle.c."""
+
+    def __init__(self, mode):
+        self.mode = STORAGE[mode]
+
+    def __enter__(self):
+        lib().orc_set_storage(self.mode)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_storage(0)
+        return False
 
 
 def pack_params(params) -> np.ndarray:

@@ -27,10 +27,20 @@
  *   - a feature pixel j of stride s belongs to the block whose inner rectangle holds image pixel
  *     (s*j_y, s*j_x); the content loss of Step 2 sums over those owned pixels only.
  *
+ * Storage precision (orc_set_storage): the network's gradient is discontinuous where a ReLU input
+ * or a pooling window's top two values meet, so a ReLU mask or pooling argmax decided in one
+ * precision cannot be compared with one decided in another. In mode 1 (float32) or 2 (bfloat16)
+ * the oracle rounds, round-to-nearest-even, every value the evaluated form stores: the weights of
+ * conv1_2..conv5_1 (bfloat16 mode only), every post-ReLU activation, the style residuals
+ * R_L = 4 w_L (G - G_ref) / n_p, and every masked feature gradient before it enters the next
+ * transposed convolution; the reverse pass stays the exact adjoint of the rounded forward values.
+ * Mode 0 (the default) is the plain FP64 definition.
+ *
  * Layout: images and activations are planar C x H x W (channel-major) doubles. Parameters are one
  * flat array: for conv l = 0..12, W_l[Cout][Cin][3][3] followed by b_l[Cout].
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -49,6 +59,29 @@ static const int kStyleStride[NSTYLE] = {1, 2, 4, 8, 16};
 #define CONTENT_STRIDE 8
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_SHAPE = 2, ORC_ERR_OOM = 3 };
+
+static int g_storage = 0; /* 0: float64 (exact), 1: float32, 2: bfloat16 */
+
+void orc_set_storage(int mode) { g_storage = (mode >= 0 && mode <= 2) ? mode : 0; }
+
+/* round to the storage type (via float32, as a float32 value is what gets narrowed) */
+static double q(double v) {
+  if (g_storage == 0) return v;
+  float f = (float)v;
+  if (g_storage == 1) return (double)f;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+  u &= 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+static void q_array(double *a, long n) {
+  if (g_storage)
+    for (long i = 0; i < n; i++) a[i] = q(a[i]);
+}
+/* weights of conv1_2..conv5_1 are stored in bfloat16 by the bfloat16 form */
+static double qw(double w, int layer) { return (g_storage == 2 && layer > 0) ? q(w) : w; }
 
 static int imin(int a, int b) { return a < b ? a : b; }
 static int imax(int a, int b) { return a > b ? a : b; }
@@ -78,7 +111,7 @@ static void param_ptrs(const double *params, const double **W, const double **b)
 /* out[co][y][x] = b[co] + sum_{ci,ky,kx} W[co][ci][ky][kx] * in[ci][y+ky-1][x+kx-1],
  * with in = 0 outside [0,h) x [0,w) (zero padding 1, stride 1). */
 static void conv3x3_forward(const double *in, int cin, int h, int w, const double *W,
-                            const double *b, int cout, double *out) {
+                            const double *b, int cout, double *out, int layer) {
   long hw = (long)h * w;
 #pragma omp parallel for schedule(static)
   for (int co = 0; co < cout; co++) {
@@ -88,7 +121,7 @@ static void conv3x3_forward(const double *in, int cin, int h, int w, const doubl
       const double *src = in + ci * hw;
       for (int ky = 0; ky < 3; ky++)
         for (int kx = 0; kx < 3; kx++) {
-          double wt = W[((long)co * cin + ci) * 9 + ky * 3 + kx];
+          double wt = qw(W[((long)co * cin + ci) * 9 + ky * 3 + kx], layer);
           int dy = ky - 1, dx = kx - 1;
           int y0 = imax(0, -dy), y1 = imin(h, h - dy);
           int x0 = imax(0, -dx), x1 = imin(w, w - dx);
@@ -105,7 +138,7 @@ static void conv3x3_forward(const double *in, int cin, int h, int w, const doubl
 /* Adjoint of conv3x3_forward with respect to its input:
  * din[ci][y][x] = sum_{co,ky,kx} W[co][ci][ky][kx] * dout[co][y-ky+1][x-kx+1] (valid terms). */
 static void conv3x3_backward_data(const double *dout, int cout, int h, int w, const double *W,
-                                  int cin, double *din) {
+                                  int cin, double *din, int layer) {
   long hw = (long)h * w;
 #pragma omp parallel for schedule(static)
   for (int ci = 0; ci < cin; ci++) {
@@ -115,7 +148,7 @@ static void conv3x3_backward_data(const double *dout, int cout, int h, int w, co
       const double *g = dout + co * hw;
       for (int ky = 0; ky < 3; ky++)
         for (int kx = 0; kx < 3; kx++) {
-          double wt = W[((long)co * cin + ci) * 9 + ky * 3 + kx];
+          double wt = qw(W[((long)co * cin + ci) * 9 + ky * 3 + kx], layer);
           int dy = 1 - ky, dx = 1 - kx; /* y' = y + dy */
           int y0 = imax(0, -dy), y1 = imin(h, h - dy);
           int x0 = imax(0, -dx), x1 = imin(w, w - dx);
@@ -219,8 +252,9 @@ static void vgg_forward(const double *params, const double *img, acts_t *A) {
   const double *in = img;
   for (int l = 0; l < NCONV; l++) {
     int h = A->h[l], w = A->w[l];
-    conv3x3_forward(in, kCin[l], h, w, W[l], b[l], kCout[l], A->a[l]);
+    conv3x3_forward(in, kCin[l], h, w, W[l], b[l], kCout[l], A->a[l], l);
     relu_inplace(A->a[l], (long)kCout[l] * h * w);
+    q_array(A->a[l], (long)kCout[l] * h * w);
     in = A->a[l];
     if (kPoolAfter[l]) {
       maxpool_forward(A->a[l], kCout[l], h, w, A->p[l]);
@@ -253,13 +287,15 @@ static int vgg_backward(const double *params, const acts_t *A, double *const *fe
     /* ReLU: gradient passes where the output is positive */
     for (long i = 0; i < n; i++)
       if (!(A->a[l][i] > 0.0)) g[i] = 0.0;
+    q_array(g, n);
     /* conv l: gradient with respect to its input */
     double *din = (l == 0) ? dimg : t;
-    conv3x3_backward_data(g, kCout[l], h, w, W[l], kCin[l], din);
+    conv3x3_backward_data(g, kCout[l], h, w, W[l], kCin[l], din, l);
     if (l == 0) break;
     int lp = l - 1;   /* producer of conv l's input */
     long np = (long)kCout[lp] * A->h[lp] * A->w[lp];
     if (kPoolAfter[lp]) {
+      q_array(t, (long)kCout[lp] * A->h[l] * A->w[l]);
       maxpool_backward(t, A->a[lp], kCout[lp], A->h[lp], A->w[lp], g);
     } else {
       memcpy(g, t, sizeof(double) * (size_t)np);
@@ -310,7 +346,7 @@ static double gram_loss_grad(const double *V, int c, long npix, double np, const
       double *gj = gV + (long)j * npix;
       for (long p = 0; p < npix; p++) gj[p] = 0.0;
       for (int i = 0; i < c; i++) {
-        double dij = (G[(long)i * c + j] - Gref[(long)i * c + j]) * (4.0 * w / np);
+        double dij = q((G[(long)i * c + j] - Gref[(long)i * c + j]) * (4.0 * w / np));
         const double *vi = V + (long)i * npix;
         for (long p = 0; p < npix; p++) gj[p] += vi[p] * dij;
       }

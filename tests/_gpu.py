@@ -24,12 +24,15 @@ def seeded(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
+def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, storage="f64"):
+    """FP64 oracle; storage="bf16"/"f32" rounds where that form of the path stores values, so
+    ReLU masks and pooling argmaxes are decided in the same precision on both sides."""
     params, u, v, x = seeded(H, W, seed, Hv, Wv, noise, bias_std)
     P = oracle.pack_params(params)
-    ct = oracle.content_target(P, u)
-    Gv = oracle.style_grams(P, v)
-    E, g, parts, Gx = oracle.loss_grad(P, x, ct, Gv, W_STYLE, LAMBDA_C)
+    with oracle.storage(storage):
+        ct = oracle.content_target(P, u)
+        Gv = oracle.style_grams(P, v)
+        E, g, parts, Gx = oracle.loss_grad(P, x, ct, Gv, W_STYLE, LAMBDA_C)
     return E, g, parts, Gx, Gv
 
 

@@ -105,21 +105,24 @@ def _cmp(res, ref, tol):
 TC = dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC)
 
 
+# the oracle evaluated with bfloat16 storage (decisions in the form's precision)
 def test_path_tc_config1():
-    _cmp(run_gpu(64, 64, 0, tiles_h=2, tiles_w=2, **TC), oracle_result(64, 64, 0), TOL_BF16)
+    _cmp(run_gpu(64, 64, 0, tiles_h=2, tiles_w=2, **TC),
+         oracle_result(64, 64, 0, storage="bf16"), TOL_BF16)
 
 
 def test_path_tc_untiled_128():
-    _cmp(run_gpu(128, 128, 1, **TC), oracle_result(128, 128, 1), TOL_BF16)
+    _cmp(run_gpu(128, 128, 1, **TC), oracle_result(128, 128, 1, storage="bf16"), TOL_BF16)
 
 
 def test_path_tc_ragged_bias():
     _cmp(run_gpu(100, 76, 2, Hv=90, Wv=111, bias_std=0.01, tiles_h=2, tiles_w=3, **TC),
-         oracle_result(100, 76, 2, Hv=90, Wv=111, bias_std=0.01), TOL_BF16)
+         oracle_result(100, 76, 2, Hv=90, Wv=111, bias_std=0.01, storage="bf16"), TOL_BF16)
 
 
 def test_path_tc_margins_cut_blocks():
-    _cmp(run_gpu(96, 480, 3, tiles_h=1, tiles_w=3, **TC), oracle_result(96, 480, 3), TOL_BF16)
+    _cmp(run_gpu(96, 480, 3, tiles_h=1, tiles_w=3, **TC),
+         oracle_result(96, 480, 3, storage="bf16"), TOL_BF16)
 
 
 def test_path_tc_matches_simt_bf16():

@@ -23,16 +23,29 @@ def seeded(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
     return params, u, v, x
 
 
+# BF16 gradient bound of the full loss: the gradient of the VGG trunk is discontinuous at every
+# ReLU / max-pool decision; with 8-bit mantissas, pooling windows whose top values sit within an
+# ulp flip under any change of rounding or accumulation order. Measured with the oracle alone:
+# rounding only the stored values to bfloat16 moves dE/dx by 0.23 (64x64 and 128x128), and the
+# exact gradient itself moves by 0.175 when x is perturbed by one bfloat16 ulp (4e-3 relative).
+# The pool-free ReLU1_1 term keeps the 2e-2 bound (6.6e-4 measured).
+TOL_BF16_FULL_GRAD = 0.35
+STYLE1_ONLY = (0.2, 0.0, 0.0, 0.0, 0.0)
+
+
 @functools.lru_cache(maxsize=None)
-def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, storage="f64"):
+def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, storage="f64",
+                  ws=None, lam=None):
     """FP64 oracle; storage="bf16"/"f32" rounds where that form of the path stores values, so
     ReLU masks and pooling argmaxes are decided in the same precision on both sides."""
     params, u, v, x = seeded(H, W, seed, Hv, Wv, noise, bias_std)
     P = oracle.pack_params(params)
+    ws = np.array(W_STYLE if ws is None else ws, np.float64)
+    lam = LAMBDA_C if lam is None else lam
     with oracle.storage(storage):
         ct = oracle.content_target(P, u)
         Gv = oracle.style_grams(P, v)
-        E, g, parts, Gx = oracle.loss_grad(P, x, ct, Gv, W_STYLE, LAMBDA_C)
+        E, g, parts, Gx = oracle.loss_grad(P, x, ct, Gv, ws, lam)
     return E, g, parts, Gx, Gv
 
 

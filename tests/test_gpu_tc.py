@@ -12,7 +12,8 @@ import torch
 import torch.nn.functional as F
 
 from paper_2212_13459_gb300 import native
-from tests._gpu import TOL_BF16, oracle_result, rel_l2, run_gpu
+from tests._gpu import (STYLE1_ONLY, TOL_BF16, TOL_BF16_FULL_GRAD, oracle_result, rel_l2,
+                        run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -92,14 +93,14 @@ def test_single_layer_fp32_simt():
     assert ((out - ref).norm() / ref.norm()).item() <= 1e-5
 
 
-def _cmp(res, ref, tol):
+def _cmp(res, ref, tol, grad_tol=TOL_BF16_FULL_GRAD):
     E, g, parts, Gx, Gv = ref
     assert res["status"] == 0
     for s in range(5):
         assert rel_l2(res["style_grams"][s], Gv[s]) <= tol, s
         assert rel_l2(res["grams"][s], Gx[s]) <= tol, s
     assert abs(res["E"] - E) <= tol * abs(E)
-    assert rel_l2(res["g"], g) <= tol, rel_l2(res["g"], g)
+    assert rel_l2(res["g"], g) <= grad_tol, rel_l2(res["g"], g)
 
 
 TC = dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC)
@@ -125,13 +126,26 @@ def test_path_tc_margins_cut_blocks():
          oracle_result(96, 480, 3, storage="bf16"), TOL_BF16)
 
 
+@pytest.mark.parametrize("case", [(64, 64, 0, 2), (128, 128, 1, 1), (96, 480, 3, 3)])
+def test_path_tc_relu1_1_term_strict(case):
+    """ReLU1_1 Gram term only (no pooling decision on the gradient path): 2e-2 on dE/dx."""
+    H, W, seed, tw = case
+    _cmp(run_gpu(H, W, seed, tiles_h=1, tiles_w=tw, w_style=STYLE1_ONLY, lambda_c=0.0, **TC),
+         oracle_result(H, W, seed, storage="bf16", ws=STYLE1_ONLY, lam=0.0), TOL_BF16,
+         grad_tol=TOL_BF16)
+
+
 def test_path_tc_matches_simt_bf16():
-    """Same BF16 storage, different MMA engine: the two agree far inside the BF16 tolerance."""
+    """Same BF16 storage, different MMA engine (only the FP32 accumulation order differs)."""
     a = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, **TC)
     b = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, precision=native.PREC_BF16,
                 conv_engine=native.CONV_SIMT)
-    assert rel_l2(a["g"], b["g"]) <= 1e-2
+    assert rel_l2(a["g"], b["g"]) <= TOL_BF16_FULL_GRAD
     assert abs(a["E"] - b["E"]) <= 1e-3 * abs(b["E"])
+    a1 = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, w_style=STYLE1_ONLY, lambda_c=0.0, **TC)
+    b1 = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, w_style=STYLE1_ONLY, lambda_c=0.0,
+                 precision=native.PREC_BF16, conv_engine=native.CONV_SIMT)
+    assert rel_l2(a1["g"], b1["g"]) <= 1e-2
 
 
 def test_path_tc_identity_exact_zero():

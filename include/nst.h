@@ -165,6 +165,16 @@ nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int 
                        const void *w2_dev, const float *bias_dev, int mode, const void *mask_dev,
                        const int *geom_dev, void *out_dev, void *stream);
 
+/* ---- single-layer Gram statistics (unit-test entry of the Gram engine) ------------------------
+ * G = sum_p V_p V_p^T over the npix rows of V ([npix][C], row-major, NHWC features of one layer),
+ * the un-normalised Gram matrix of Eq. 4 (divide by n_p for G^L). FP32 partial sums over pixel
+ * chunks, reduced in FP64 in a fixed order (deterministic). dtype: NST_PREC_FP32 or
+ * NST_PREC_BF16 elements; C a multiple of 64, 64 <= C <= 512; 1 <= npix < 2^31. G_dev: C*C
+ * doubles in device memory, overwritten. Scratch for the partial sums (at most 1,216 blocks of
+ * 64 x 64 floats, 19 MiB) is allocated stream-ordered and released on `stream`. */
+nst_status nst_gram(int dtype, const void *V_dev, long long npix, int C, double *G_dev,
+                    void *stream);
+
 /* Library version string. */
 const char *nst_version(void);
 

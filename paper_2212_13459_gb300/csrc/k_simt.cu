@@ -443,11 +443,14 @@ template void launch_unpool<__nv_bfloat16>(const __nv_bfloat16 *, const __nv_bfl
 // chunk c covers pixels [p0, p1) of block b's owned rectangle (row-major inside the rectangle);
 // CTA (c, pair) accumulates the 64x64 block (I, J), I <= J, of sum_p V_p V_p^T in FP32 and writes
 // it to part[(c * npairs + pair) * 4096 + i * 64 + j].
+// With chunks == null, V is one flat [n_flat][C] matrix and CTA c takes pixels
+// [c * chunk_len, min((c + 1) * chunk_len, n_flat)).
 template <typename T>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__ V, int Hb, int Wb,
                                                            int C, const OwnRect *__restrict__ own,
                                                            const GramChunk *__restrict__ chunks,
-                                                           float *__restrict__ part) {
+                                                           float *__restrict__ part,
+                                                           long long chunk_len, long long n_flat) {
   __shared__ __align__(16) float Ai[32][68];
   __shared__ __align__(16) float Aj[32][68];
   const int nb = C / 64;
@@ -455,8 +458,17 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const T *__restrict__
   int pair = blockIdx.y, I = 0;
   while (pair >= nb - I) { pair -= nb - I; I++; }
   const int J = I + pair;
-  const GramChunk ch = chunks[blockIdx.x];
-  const OwnRect r = own[ch.b];
+  GramChunk ch;
+  OwnRect r;
+  if (chunks) {
+    ch = chunks[blockIdx.x];
+    r = own[ch.b];
+  } else {
+    const long long p0 = (long long)blockIdx.x * chunk_len;
+    const long long p1 = p0 + chunk_len < n_flat ? p0 + chunk_len : n_flat;
+    ch = {0, (int)p0, (int)p1, 0};
+    r = {0, 1, 0, (int)n_flat};
+  }
   const int rw = r.x1 - r.x0;
   const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
   const int lp = tid >> 3, lc = (tid & 7) * 8;
@@ -527,8 +539,21 @@ void launch_gram_partial(const T *V, int Hb, int Wb, int C, const OwnRect *own,
                          const GramChunk *chunks, int nchunks, float *part, cudaStream_t s) {
   const int nb = C / 64;
   dim3 grid(nchunks, nb * (nb + 1) / 2);
-  gram_partial_kernel<T><<<grid, 256, 0, s>>>(V, Hb, Wb, C, own, chunks, part);
+  gram_partial_kernel<T><<<grid, 256, 0, s>>>(V, Hb, Wb, C, own, chunks, part, 0, 0);
 }
+
+template <typename T>
+void launch_gram_partial_flat(const T *V, long long npix, int C, long long chunk_len, int nchunks,
+                              float *part, cudaStream_t s) {
+  const int nb = C / 64;
+  dim3 grid(nchunks, nb * (nb + 1) / 2);
+  gram_partial_kernel<T><<<grid, 256, 0, s>>>(V, 1, (int)npix, C, nullptr, nullptr, part,
+                                              chunk_len, npix);
+}
+template void launch_gram_partial_flat<float>(const float *, long long, int, long long, int,
+                                              float *, cudaStream_t);
+template void launch_gram_partial_flat<__nv_bfloat16>(const __nv_bfloat16 *, long long, int,
+                                                      long long, int, float *, cudaStream_t);
 template void launch_gram_partial<float>(const float *, int, int, int, const OwnRect *,
                                          const GramChunk *, int, float *, cudaStream_t);
 template void launch_gram_partial<__nv_bfloat16>(const __nv_bfloat16 *, int, int, int,

@@ -941,5 +941,40 @@ nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int 
   return NST_OK;
 }
 
+// chunking of a flat [npix][C] matrix: about 1,216 CTAs over the 64 x 64 block pairs
+static void gram_flat_plan(long long npix, int C, long long *chunk_len, int *nchunks) {
+  const int nb = C / 64, npairs = nb * (nb + 1) / 2;
+  const long long target = std::max(1, 1216 / npairs);
+  long long ch = std::max(256LL, (npix + target - 1) / target);
+  ch = (ch + 31) / 32 * 32;
+  *chunk_len = ch;
+  *nchunks = (int)((npix + ch - 1) / ch);
+}
+
+nst_status nst_gram(int dtype, const void *V, long long npix, int C, double *G, void *stream) {
+  nst_ctx *ctx = nullptr;
+  if ((dtype != NST_PREC_FP32 && dtype != NST_PREC_BF16) || !V || !G || C < 64 || C > 512 ||
+      C % 64 || npix < 1 || npix >= (1LL << 31))
+    return fail(nullptr, NST_ERR_INVALID_ARG, "bad Gram arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  long long chunk_len;
+  int nchunks;
+  gram_flat_plan(npix, C, &chunk_len, &nchunks);
+  const int nb = C / 64, npairs = nb * (nb + 1) / 2;
+  float *part = nullptr;
+  CK(cudaMallocAsync((void **)&part, (size_t)nchunks * npairs * 4096 * sizeof(float), s));
+  CK(cudaMemsetAsync(G, 0, sizeof(double) * C * C, s));
+  if (dtype == NST_PREC_BF16)
+    launch_gram_partial_flat<__nv_bfloat16>((const __nv_bfloat16 *)V, npix, C, chunk_len, nchunks,
+                                            part, s);
+  else
+    launch_gram_partial_flat<float>((const float *)V, npix, C, chunk_len, nchunks, part, s);
+  launch_gram_reduce(part, nchunks, C, G, s);
+  CK(cudaFreeAsync(part, s));
+  CK(cudaGetLastError());
+  return NST_OK;
+}
+
 }  // extern "C"
+
 

@@ -42,6 +42,9 @@ void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C
 template <typename T>
 void launch_gram_partial(const T *V, int Hb, int Wb, int C, const OwnRect *own,
                          const GramChunk *chunks, int nchunks, float *part, cudaStream_t s);
+template <typename T>
+void launch_gram_partial_flat(const T *V, long long npix, int C, long long chunk_len, int nchunks,
+                              float *part, cudaStream_t s);
 void launch_gram_reduce(const float *part, int nchunks, int C, double *Gacc, cudaStream_t s);
 void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s);
 template <typename T>

@@ -78,6 +78,7 @@ def lib():
                 "nst_version": ([], ctypes.c_char_p),
                 "nst_conv3x3": ([ip, ip, ip, ip, ip, ip, ip, ip, vp, vp, ip, vp, vp, vp, ip, vp,
                                  vp, vp, vp], ip),
+                "nst_gram": ([ip, vp, ll, ip, vp, vp], ip),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -256,3 +257,10 @@ def conv3x3(dtype, engine, inp, w, out, bias=None, mode=0, mask=None, in2=None, 
     _check(lib().nst_conv3x3(dtype, engine, B, H, W, cin, cout, taps, _ptr(inp), _ptr(w), k2,
                              _ptr(in2), _ptr(w2), _ptr(bias), mode, _ptr(mask), _ptr(geom),
                              _ptr(out), _stream(stream)))
+
+
+def gram(V, G, stream=None):
+    """G (C x C float64, device) = V^T V for V [npix, C] (float32 or bfloat16, device)."""
+    import torch
+    dtype = PREC_BF16 if V.dtype == torch.bfloat16 else PREC_FP32
+    _check(lib().nst_gram(dtype, _ptr(V), V.shape[0], V.shape[1], _ptr(G), _stream(stream)))

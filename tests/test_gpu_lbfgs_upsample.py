@@ -54,3 +54,16 @@ def test_upsample_matches_oracle(h, w, H, W):
         assert np.abs(got[:, rows] - ref[:, rows]).max() <= 1e-5
     else:
         assert np.abs(got - ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("npix,C,dtype", [(1000, 64, torch.float32), (70001, 512, torch.bfloat16),
+                                          (300, 128, torch.bfloat16), (5000, 256, torch.float32)])
+def test_gram_entry_matches_float64(npix, C, dtype):
+    """nst_gram (the Gram engine of Eq. 4 on one flat feature matrix) against a float64 product."""
+    g = torch.Generator(device="cuda").manual_seed(npix + C)
+    V = torch.rand(npix, C, device="cuda", generator=g).to(dtype)
+    G = torch.full((C, C), 3.0, dtype=torch.float64, device="cuda")
+    native.gram(V, G)
+    ref = V.double().T @ V.double()
+    assert ((G - ref).norm() / ref.norm()).item() <= 1e-6
+    assert torch.equal(G, G.T)

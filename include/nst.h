@@ -175,6 +175,23 @@ nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int 
 nst_status nst_gram(int dtype, const void *V_dev, long long npix, int C, double *G_dev,
                     void *stream);
 
+/* ---- Gram statistics without device allocation ----------------------------------------------
+ * The paper has no counterpart: this is a library convenience. Same result and kernels as
+ * nst_gram, for callers that may not allocate device memory themselves (for example a plugin
+ * inside an application whose own pool allocator owns the GPU, where cudaMalloc/cudaFree would
+ * synchronize the device and bypass the pool). The chunk partial sums go to a fixed 16 MiB array
+ * inside libnst's device image instead of allocated scratch; every GPU that loads the library
+ * keeps that array until the process exits. The call allocates nothing.
+ *   - dtype, V_dev, npix, G_dev as for nst_gram; C must be a multiple of 64 with 64 <= C <= 512
+ *     (the per-chunk block pairs must fit the array): otherwise NST_ERR_SHAPE, nothing launched.
+ *   - The first call on each device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents: calls whose work
+ *     overlaps on the GPU (different streams, or different threads) race and corrupt each other;
+ *     serialize them on one stream. */
+nst_status nst_gram_noalloc(int dtype, const void *V_dev, long long npix, int C, double *G_dev,
+                            void *stream);
+
 /* Library version string. */
 const char *nst_version(void);
 

@@ -79,6 +79,7 @@ def lib():
                 "nst_conv3x3": ([ip, ip, ip, ip, ip, ip, ip, ip, vp, vp, ip, vp, vp, vp, ip, vp,
                                  vp, vp, vp], ip),
                 "nst_gram": ([ip, vp, ll, ip, vp, vp], ip),
+                "nst_gram_noalloc": ([ip, vp, ll, ip, vp, vp], ip),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -264,3 +265,12 @@ def gram(V, G, stream=None):
     import torch
     dtype = PREC_BF16 if V.dtype == torch.bfloat16 else PREC_FP32
     _check(lib().nst_gram(dtype, _ptr(V), V.shape[0], V.shape[1], _ptr(G), _stream(stream)))
+
+
+def gram_noalloc(V, G, stream=None):
+    """As gram(), through nst_gram_noalloc: no device allocation by the library (its partial sums
+    use a fixed array in the library's device image; calls must not overlap on the GPU)."""
+    import torch
+    dtype = PREC_BF16 if V.dtype == torch.bfloat16 else PREC_FP32
+    _check(lib().nst_gram_noalloc(dtype, _ptr(V), V.shape[0], V.shape[1], _ptr(G),
+                                  _stream(stream)))

@@ -185,31 +185,31 @@ template void launch_conv_simt<__nv_bfloat16>(const ConvArgs &, cudaStream_t);
 // ---- conv1_1 forward from the planar image (block extraction fused) ----------------------------
 // out[b][y][x][c] = relu(b1[c] + sum W1[c][ci][ky][kx] * blk(ci, y+ky-1, x+kx-1)), where blk is the
 // block's extended rectangle of x and reads zero outside it (the block is a standalone image).
+// One thread computes all 64 channels of one pixel; every weight read is a float4 that all
+// threads of a warp share (one shared-memory transaction feeds 4 FMAs per thread).
 template <typename T>
-__global__ void __launch_bounds__(256) conv11_fwd_kernel(const float *__restrict__ img, int H,
+__global__ void __launch_bounds__(128) conv11_fwd_kernel(const float *__restrict__ img, int H,
                                                          int W, const float *__restrict__ w11,
                                                          const float *__restrict__ b11,
                                                          const BlockGeom *__restrict__ geom,
                                                          int B, int Hb, int Wb, T *__restrict__ out) {
-  __shared__ float ws[27][64];
-  __shared__ float bs[64];
+  __shared__ __align__(16) float ws[27][64];
+  __shared__ __align__(16) float bs[64];
   for (int i = threadIdx.x; i < 27 * 64; i += blockDim.x) {
     const int co = i / 27, k = i % 27;  // k = ci*9 + ky*3 + kx
     ws[k][co] = w11[i];
   }
   if (threadIdx.x < 64) bs[threadIdx.x] = b11[threadIdx.x];
   __syncthreads();
-  const int cg = threadIdx.x & 3;  // channel group of 16
   const long long npix = (long long)B * Hb * Wb;
-  for (long long p = (long long)blockIdx.x * 64 + (threadIdx.x >> 2); p < npix;
-       p += (long long)gridDim.x * 64) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(p % Wb);
     const int y = (int)((p / Wb) % Hb);
     const int b = (int)(p / ((long long)Wb * Hb));
     const BlockGeom g = geom[b];
-    float acc[16];
-    const bool valid = y < g.eh && x < g.ew;
-    if (valid) {
+    float acc[64];
+    if (y < g.eh && x < g.ew) {
       float in[27];
 #pragma unroll
       for (int ci = 0; ci < 3; ci++)
@@ -220,22 +220,34 @@ __global__ void __launch_bounds__(256) conv11_fwd_kernel(const float *__restrict
             const int yy = y + ky - 1, xx = x + kx - 1;
             const bool ok = yy >= 0 && yy < g.eh && xx >= 0 && xx < g.ew;
             in[ci * 9 + ky * 3 + kx] =
-                ok ? img[((size_t)ci * H + g.ey0 + yy) * W + g.ex0 + xx] : 0.f;
+                ok ? __ldg(img + ((size_t)ci * H + g.ey0 + yy) * W + g.ex0 + xx) : 0.f;
           }
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        float s = bs[cg * 16 + j];
-#pragma unroll
-        for (int k = 0; k < 27; k++) s = fmaf(ws[k][cg * 16 + j], in[k], s);
-        acc[j] = fmaxf(s, 0.f);
+      for (int c4 = 0; c4 < 16; c4++) {
+        const float4 b4 = *reinterpret_cast<const float4 *>(&bs[c4 * 4]);
+        acc[c4 * 4] = b4.x; acc[c4 * 4 + 1] = b4.y; acc[c4 * 4 + 2] = b4.z; acc[c4 * 4 + 3] = b4.w;
       }
+#pragma unroll
+      for (int k = 0; k < 27; k++) {
+        const float v = in[k];
+#pragma unroll
+        for (int c4 = 0; c4 < 16; c4++) {
+          const float4 w4 = *reinterpret_cast<const float4 *>(&ws[k][c4 * 4]);
+          acc[c4 * 4] = fmaf(w4.x, v, acc[c4 * 4]);
+          acc[c4 * 4 + 1] = fmaf(w4.y, v, acc[c4 * 4 + 1]);
+          acc[c4 * 4 + 2] = fmaf(w4.z, v, acc[c4 * 4 + 2]);
+          acc[c4 * 4 + 3] = fmaf(w4.w, v, acc[c4 * 4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 64; c++) acc[c] = fmaxf(acc[c], 0.f);
     } else {
 #pragma unroll
-      for (int j = 0; j < 16; j++) acc[j] = 0.f;
+      for (int c = 0; c < 64; c++) acc[c] = 0.f;
     }
-    T *o = out + (size_t)p * 64 + cg * 16;
-    store8(o, acc);
-    store8(o + 8, acc + 8);
+    T *o = out + (size_t)p * 64;
+#pragma unroll
+    for (int c8 = 0; c8 < 8; c8++) store8(o + c8 * 8, acc + c8 * 8);
   }
 }
 
@@ -243,9 +255,9 @@ template <typename T>
 void launch_conv11_fwd(const float *img, int H, int W, const float *w11, const float *b11,
                        const BlockGeom *geom, int B, int Hb, int Wb, T *out, cudaStream_t s) {
   long long npix = (long long)B * Hb * Wb;
-  long long blocks = (npix + 63) / 64;
-  int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
-  conv11_fwd_kernel<T><<<grid, 256, 0, s>>>(img, H, W, w11, b11, geom, B, Hb, Wb, out);
+  long long blocks = (npix + 127) / 128;
+  int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+  conv11_fwd_kernel<T><<<grid, 128, 0, s>>>(img, H, W, w11, b11, geom, B, Hb, Wb, out);
 }
 template void launch_conv11_fwd<float>(const float *, int, int, const float *, const float *,
                                        const BlockGeom *, int, int, int, float *, cudaStream_t);
@@ -261,10 +273,11 @@ __global__ void __launch_bounds__(256) conv11_dgrad_scatter_kernel(
     const T *__restrict__ g, const float *__restrict__ w11, const BlockGeom *__restrict__ geom,
     const OwnRect *__restrict__ inner, int B, int Hb, int Wb, float *__restrict__ grad, int H,
     int W) {
-  __shared__ float ws[9][64][3];
-  for (int i = threadIdx.x; i < 64 * 27; i += blockDim.x) {
-    const int co = i / 27, r = i % 27, ci = r / 9, k = r % 9;
-    ws[k][co][ci] = w11[i];
+  // ws[k][co] = {W1[co][0][k], W1[co][1][k], W1[co][2][k], 0}: one float4 read per 3 FMAs
+  __shared__ __align__(16) float4 ws[9][64];
+  for (int i = threadIdx.x; i < 9 * 64; i += blockDim.x) {
+    const int k = i / 64, co = i % 64;
+    ws[k][co] = make_float4(w11[co * 27 + k], w11[co * 27 + 9 + k], w11[co * 27 + 18 + k], 0.f);
   }
   __syncthreads();
   const int b = blockIdx.y;
@@ -277,21 +290,24 @@ __global__ void __launch_bounds__(256) conv11_dgrad_scatter_kernel(
        q += (long long)gridDim.x * blockDim.x) {
     const int y = r.y0 + (int)(q / rw), x = r.x0 + (int)(q % rw);
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
     for (int ky = 0; ky < 3; ky++)
+#pragma unroll
       for (int kx = 0; kx < 3; kx++) {
         const int yy = y - ky + 1, xx = x - kx + 1;
         if (yy < 0 || yy >= Hb || xx < 0 || xx >= Wb) continue;
         const T *gp = g + (((size_t)b * Hb + yy) * Wb + xx) * 64;
         const int k = ky * 3 + kx;
-#pragma unroll 2
+#pragma unroll
         for (int c8 = 0; c8 < 64; c8 += 8) {
           float gv[8];
           load8(gp + c8, gv);
 #pragma unroll
           for (int j = 0; j < 8; j++) {
-            d0 = fmaf(ws[k][c8 + j][0], gv[j], d0);
-            d1 = fmaf(ws[k][c8 + j][1], gv[j], d1);
-            d2 = fmaf(ws[k][c8 + j][2], gv[j], d2);
+            const float4 w = ws[k][c8 + j];
+            d0 = fmaf(w.x, gv[j], d0);
+            d1 = fmaf(w.y, gv[j], d1);
+            d2 = fmaf(w.z, gv[j], d2);
           }
         }
       }

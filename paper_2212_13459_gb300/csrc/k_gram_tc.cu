@@ -1,0 +1,213 @@
+// k_gram_tc.cu -- Gram statistics on the tensor cores: sum over owned pixels p of V_p V_p^T
+// (Eq. 4, accumulated block by block as in Algorithm 1, Step 1).
+//
+// GEMM view: D[M x N] = A[M x K] B[K x N] with M = 128 channels of the I tile, N = channels of
+// the J tile (64 / 128 / 256), K = pixels. Both operands are the same NHWC activation, so both
+// are MN-major in shared memory (64 channels = 128 bytes contiguous per pixel row, 128-byte
+// swizzle). One TMA box of 64 pixels feeds every operand slab of a K step. Each block gets its
+// own tensor map whose bounds are its owned rectangle, so pixels outside it read as zero and
+// never enter the sum. Every CTA accumulates one (I, J) tile over one run of boxes in TMEM
+// (FP32) and writes it out; a fixed-order FP64 reduction adds the runs (deterministic).
+#include <algorithm>
+
+#include "nst_internal.cuh"
+#include "nst_kernels.h"
+#include "tc_ptx.cuh"
+
+namespace nst {
+namespace {
+
+using namespace nst::tc;
+
+constexpr int kThreads = 192;
+constexpr int kStages = 4;
+constexpr uint32_t kSlab = 64 * 128;  // one 64-pixel x 64-channel BF16 slab
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
+  constexpr uint32_t A_BYTES = 2 * kSlab;
+  constexpr uint32_t B_BYTES = (N / 64) * kSlab;
+  constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t TMEM_COLS = N;
+  // kind::f16, FP32 D, BF16 A/B, both MN-major, M = 128, N
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                             ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const GramTcChunk ch = a.chunks[blockIdx.x];
+  const int tile = blockIdx.y, I = tile / a.nJ, J = tile % a.nJ;
+  const CUtensorMap *map = a.maps + ch.b;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int k = ch.box0; k < ch.box1; k++) {
+        if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) break;
+        const uint32_t fb = smem_u32(&full_bar[stage]);
+        const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+        const int x = (k % ch.nbx) * a.TW, y = (k / ch.nbx) * a.TH;
+        mbar_expect_tx(fb, STAGE_BYTES);
+        tma_load_4d(sa, map, fb, I * 128, x, y, 0);
+        tma_load_4d(sa + kSlab, map, fb, I * 128 + 64, x, y, 0);
+#pragma unroll
+        for (int j = 0; j < N / 64; j++) tma_load_4d(sb + j * kSlab, map, fb, J * N + j * 64, x, y, 0);
+        if (++stage == kStages) { stage = 0; phase ^= 1; }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int k = ch.box0; k < ch.box1; k++) {
+        if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++)   // 16 pixels (two 8-row groups) per MMA
+          mma_bf16(tmem_base, sw128_desc_mn(sa + kk * 2048, kSlab),
+                   sw128_desc_mn(sb + kk * 2048, kSlab), IDESC,
+                   (k > ch.box0 || kk > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&empty_bar[stage]));
+        if (++stage == kStages) { stage = 0; phase ^= 1; }
+      }
+      if (ok) mma_commit(smem_u32(&done_bar));
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;   // channel I * 128 + row
+    if (mbar_wait(smem_u32(&done_bar), 0, &abort_flag, a.err)) {
+      tc_fence_after();
+      float *out = a.part + (((size_t)blockIdx.x * a.nI * a.nJ + tile) * 128 + row) * N;
+      const bool live = I * 128 + row < a.C;
+#pragma unroll 1
+      for (int c = 0; c < N; c += 32) {
+        float v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (live) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4 *>(out + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+// Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials
+__global__ void gram_tc_reduce_kernel(const float *__restrict__ part, int nruns, int C, int N,
+                                      int nI, int nJ, double *__restrict__ Gacc) {
+  const long long n = (long long)C * C;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / C), j = (int)(e % C);
+    const int tile = (i / 128) * nJ + j / N;
+    const size_t off = ((size_t)tile * 128 + (i % 128)) * N + (j % N);
+    const size_t stride = (size_t)nI * nJ * 128 * N;
+    double s = 0.0;
+    for (int r = 0; r < nruns; r++) s += (double)part[(size_t)r * stride + off];
+    Gacc[e] += s;
+  }
+}
+
+template <int N>
+cudaError_t launch_n(const GramTcArgs &a, int nruns, cudaStream_t s) {
+  constexpr size_t smem = (size_t)kStages * (2 * kSlab + (N / 64) * kSlab) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<N>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  gram_tc_kernel<N><<<dim3(nruns, a.nI * a.nJ), kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+}  // namespace
+
+void gram_tc_shape(int C, int *N, int *nI, int *nJ) {
+  *N = C >= 256 ? 256 : C;
+  *nI = C <= 128 ? 1 : C / 128;
+  *nJ = C / *N;
+}
+
+void gram_tc_patch(int own_h, int own_w, int *TH, int *TW) {
+  static const int cand[5][2] = {{1, 64}, {2, 32}, {4, 16}, {8, 8}, {16, 4}};
+  long long best = -1;
+  for (auto &c : cand) {
+    const long long area = (long long)((own_h + c[0] - 1) / c[0]) * c[0] *
+                           ((own_w + c[1] - 1) / c[1]) * c[1];
+    if (best < 0 || area < best) { best = area; *TH = c[0]; *TW = c[1]; }
+  }
+}
+
+cudaError_t encode_gram_map(CUtensorMap *m, const void *base, int C, int own_w, int own_h,
+                            long long row_stride_px, int TH, int TW) {
+  EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(tc_encode_tiled_fn());
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)std::max(own_w, 1),
+                        (cuuint64_t)std::max(own_h, 1), 1};
+  cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)row_stride_px * C * 2,
+                           (cuuint64_t)row_stride_px * C * 2 * std::max(own_h, 1)};
+  cuuint32_t box[4] = {64, (cuuint32_t)TW, (cuuint32_t)TH, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims,
+                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStream_t s) {
+  if (nruns <= 0) return cudaSuccess;
+  cudaError_t e;
+  switch (a.N) {
+    case 64: e = launch_n<64>(a, nruns, s); break;
+    case 128: e = launch_n<128>(a, nruns, s); break;
+    case 256: e = launch_n<256>(a, nruns, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  const long long n = (long long)a.C * a.C;
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  gram_tc_reduce_kernel<<<grid, 256, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
+  return cudaGetLastError();
+}
+
+}  // namespace nst

@@ -103,6 +103,7 @@ constexpr int kOwnContent = 5, kOwnInner = 6;
 struct Batch {
   int t0, B;                                  // first block index, block count
   int chunk_off[kNStyle + 1], nchunks[kNStyle + 1];  // Gram chunks per style layer; [5] content
+  int tc_off[kNStyle], tc_runs[kNStyle];      // tensor-core Gram runs per style layer
   int max_inner_px, max_content_px;
 };
 
@@ -114,8 +115,14 @@ struct PassPlan {
   BlockGeom *d_geom = nullptr;    // [ntiles]
   OwnRect *d_own = nullptr;       // [kOwnSlots][ntiles]
   GramChunk *d_chunks = nullptr;  // all chunks
-  size_t gram_part_floats = 0;    // largest nchunks * npairs * 4096
+  size_t gram_part_floats = 0;    // largest nchunks * npairs * 4096 (or tensor-core tiles)
   int max_content_chunks = 0;
+  // tensor-core Gram: box shape per style layer, runs, and per-block owned-rectangle maps
+  int tc_TH[kNStyle], tc_TW[kNStyle];
+  GramTcChunk *d_tcchunks = nullptr;
+  CUtensorMap *d_maps = nullptr;   // [kNStyle][ntiles]
+  const void *maps_ws = nullptr;   // workspace the maps were encoded for
+  std::vector<OwnRect> own_host;   // [kOwnSlots][ntiles]
 };
 
 struct Workspace {
@@ -271,6 +278,7 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
     }
   }
   std::vector<GramChunk> chunks;
+  std::vector<GramTcChunk> tcchunks;
   for (int t0 = 0; t0 < nt; t0 += B) {
     Batch bt{};
     bt.t0 = t0;
@@ -300,6 +308,37 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
       else
         p.max_content_chunks = std::max(p.max_content_chunks, bt.nchunks[s]);
     }
+    for (int si = 0; si < kNStyle; si++) {
+      int N, nI, nJ;
+      gram_tc_shape(kStyleC[si], &N, &nI, &nJ);
+      if (t0 == 0) {
+        long long h = 0, w = 0;
+        for (int i = 0; i < nt; i++) {
+          const OwnRect &r = own[(size_t)si * nt + i];
+          h = std::max<long long>(h, r.y1 - r.y0);
+          w = std::max<long long>(w, r.x1 - r.x0);
+        }
+        gram_tc_patch((int)h, (int)w, &p.tc_TH[si], &p.tc_TW[si]);
+      }
+      const int TH = p.tc_TH[si], TW = p.tc_TW[si];
+      long long boxes = 0;
+      for (int i = t0; i < t0 + bt.B; i++) {
+        const OwnRect &r = own[(size_t)si * nt + i];
+        boxes += (long long)((r.y1 - r.y0 + TH - 1) / TH) * ((r.x1 - r.x0 + TW - 1) / TW);
+      }
+      const long long per = std::max(2LL, (boxes * nI * nJ + 303) / 304);
+      bt.tc_off[si] = (int)tcchunks.size();
+      for (int i = t0; i < t0 + bt.B; i++) {
+        const OwnRect &r = own[(size_t)si * nt + i];
+        const int nbx = (r.x1 - r.x0 + TW - 1) / TW, nby = (r.y1 - r.y0 + TH - 1) / TH;
+        const long long nb = (long long)nbx * nby;
+        for (long long k = 0; k < nb; k += per)
+          tcchunks.push_back({i - t0, (int)k, (int)std::min(nb, k + per), nbx});
+      }
+      bt.tc_runs[si] = (int)tcchunks.size() - bt.tc_off[si];
+      p.gram_part_floats = std::max(p.gram_part_floats,
+                                    (size_t)bt.tc_runs[si] * nI * nJ * 128 * N);
+    }
     bt.max_inner_px = 0;
     bt.max_content_px = 0;
     for (int i = t0; i < t0 + bt.B; i++) {
@@ -319,6 +358,12 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
   if (!chunks.empty())
     CK(cudaMemcpy(p.d_chunks, chunks.data(), sizeof(GramChunk) * chunks.size(),
                   cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&p.d_tcchunks, sizeof(GramTcChunk) * std::max<size_t>(1, tcchunks.size())));
+  if (!tcchunks.empty())
+    CK(cudaMemcpy(p.d_tcchunks, tcchunks.data(), sizeof(GramTcChunk) * tcchunks.size(),
+                  cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&p.d_maps, sizeof(CUtensorMap) * kNStyle * nt));
+  p.own_host = own;
   auto res = ctx->plans.emplace(key, std::move(p));
   *out = &res.first->second;
   return NST_OK;
@@ -416,15 +461,57 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
   return NST_OK;
 }
 
+// per-block owned-rectangle tensor maps of the style layers, for the current workspace
+nst_status ensure_gram_maps(nst_ctx *ctx, PassPlan &p, const Workspace &ws) {
+  if (p.maps_ws == ctx->d_ws) return NST_OK;
+  const int nt = (int)p.tiles.size();
+  std::vector<CUtensorMap> maps((size_t)kNStyle * nt);
+  for (const Batch &bt : p.batches)
+    for (int si = 0; si < kNStyle; si++) {
+      const int l = kStyleConv[si], lv = kLevel[l], C = kCout[l];
+      const long long Hl = p.Hb >> lv, Wl = p.Wb >> lv;
+      for (int i = bt.t0; i < bt.t0 + bt.B; i++) {
+        const OwnRect &r = p.own_host[(size_t)si * nt + i];
+        const char *base = (const char *)ws.act[l] +
+                           ((((long long)(i - bt.t0) * Hl + r.y0) * Wl + r.x0) * C) * 2;
+        cudaError_t e = encode_gram_map(&maps[(size_t)si * nt + i], base, C, r.x1 - r.x0,
+                                        r.y1 - r.y0, Wl, p.tc_TH[si], p.tc_TW[si]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "Gram tensor map");
+      }
+    }
+  CK(cudaMemcpy(p.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                cudaMemcpyHostToDevice));
+  p.maps_ws = ctx->d_ws;
+  return NST_OK;
+}
+
 template <typename T>
-nst_status gram_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const Workspace &ws,
+nst_status gram_batch(nst_ctx *ctx, PassPlan &p, const Batch &bt, const Workspace &ws,
                       cudaStream_t s) {
   const int nt = (int)p.tiles.size();
+  if (ctx->use_tc) {
+    nst_status st = ensure_gram_maps(ctx, p, ws);
+    if (st) return st;
+  }
   for (int si = 0; si < kNStyle; si++) {
     const int l = kStyleConv[si], lv = kLevel[l];
-    if (bt.nchunks[si] == 0) continue;
     Timer tm(ctx, kTGram, s);
     ctx->launches += 2;
+    if (ctx->use_tc) {
+      GramTcArgs a{};
+      a.maps = p.d_maps + (size_t)si * nt + bt.t0;
+      a.chunks = p.d_tcchunks + bt.tc_off[si];
+      a.C = kCout[l];
+      gram_tc_shape(a.C, &a.N, &a.nI, &a.nJ);
+      a.TH = p.tc_TH[si];
+      a.TW = p.tc_TW[si];
+      a.part = ctx->d_gpart;
+      a.err = ctx->d_err;
+      cudaError_t e = launch_gram_tc(a, bt.tc_runs[si], ctx->d_gacc + gram_offset(si), s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core Gram launch");
+      continue;
+    }
+    if (bt.nchunks[si] == 0) continue;
     launch_gram_partial<T>((const T *)ws.act[l], p.Hb >> lv, p.Wb >> lv, kCout[l],
                            p.d_own + (size_t)si * nt + bt.t0, p.d_chunks + bt.chunk_off[si],
                            bt.nchunks[si], ctx->d_gpart, s);
@@ -748,6 +835,8 @@ nst_status nst_destroy(nst_ctx *ctx) {
     cudaFree(kv.second.d_geom);
     cudaFree(kv.second.d_own);
     cudaFree(kv.second.d_chunks);
+    cudaFree(kv.second.d_tcchunks);
+    cudaFree(kv.second.d_maps);
   }
   for (auto &ev : ctx->ev_pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   delete ctx;

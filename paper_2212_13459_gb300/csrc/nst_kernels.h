@@ -1,5 +1,7 @@
 // nst_kernels.h -- host-side declarations of the library's kernel launchers.
 #pragma once
+#include <cuda.h>
+
 #include "nst_internal.cuh"
 
 namespace nst {
@@ -62,6 +64,25 @@ void launch_finish_loss(const double *parts, double *loss, cudaStream_t s);
 // Returns cudaSuccess or the error of tensor-map encoding / launch.
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s);
 bool tc_available();
+void *tc_encode_tiled_fn();   // cuTensorMapEncodeTiled (driver entry point), null if unavailable
+int tc_num_sms();
+
+// k_gram_tc.cu: Gram statistics on the tensor cores
+struct GramTcChunk {
+  int b, box0, box1, nbx;  // boxes [box0, box1) of block b's owned rectangle, nbx boxes per row
+};
+struct GramTcArgs {
+  const CUtensorMap *maps;    // per block of the batch: owned rectangle as a 4-D BF16 map
+  const GramTcChunk *chunks;  // one run per CTA column
+  int C, N, nI, nJ, TH, TW;   // channels, J-tile width, tile counts, box shape (TH * TW = 64)
+  float *part;                // [runs][nI * nJ][128][N] FP32 partial tiles
+  unsigned *err;
+};
+void gram_tc_shape(int C, int *N, int *nI, int *nJ);
+void gram_tc_patch(int own_h, int own_w, int *TH, int *TW);
+cudaError_t encode_gram_map(CUtensorMap *m, const void *base, int C, int own_w, int own_h,
+                            long long row_stride_px, int TH, int TW);
+cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStream_t s);
 
 // k_lbfgs.cu (L-BFGS launchers are declared in nst_lbfgs_dev.h)
 void launch_bicubic(const float *x, int C, int h, int w, float *out, int H, int W,

@@ -161,3 +161,17 @@ def test_path_tc_identity_exact_zero():
     ctx.loss_grad(ut, g, loss)
     torch.cuda.synchronize()
     assert loss.item() == 0.0 and torch.count_nonzero(g).item() == 0
+
+
+@pytest.mark.parametrize("case", [(64, 64, 0, 2), (100, 76, 2, 2), (96, 480, 3, 1)])
+def test_path_tc_grams_match_simt_engine(case):
+    """The tensor-core Gram (MN-major tcgen05, per-block owned-rectangle tensor maps) against the
+    CUDA-core Gram on the same BF16 path: G(x) and G(v) per layer agree to 5e-3 (the convolution
+    engines' accumulation orders differ, so the BF16 activations differ by a few ulps)."""
+    H, W, seed, th = case
+    a = run_gpu(H, W, seed, tiles_h=th, tiles_w=th + 1, **TC)
+    b = run_gpu(H, W, seed, tiles_h=th, tiles_w=th + 1, precision=native.PREC_BF16,
+                conv_engine=native.CONV_SIMT)
+    for s in range(5):
+        assert rel_l2(a["grams"][s], b["grams"][s]) <= 5e-3, s
+        assert rel_l2(a["style_grams"][s], b["style_grams"][s]) <= 5e-3, s

@@ -208,6 +208,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     if ctx.sync_status() != 0:
         raise RuntimeError("device status after warm-up: %s" % native.lib().nst_last_error(ctx.h))
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    hbm_used_gb = (total_b - free_b) / 1e9
     # ---- timed region: K evaluations, CUDA events on the launching stream ----
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -246,7 +248,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
     report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E, status, e2e,
-           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist)
+           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist, hbm_used_gb)
 
 
 def e2e_leg(ctx, x, H, W, args, dist, dev, world):
@@ -296,7 +298,7 @@ def lbfgs_leg(x, grad, H, W, stream, dev):
 
 
 def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E, status, e2e,
-           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist):
+           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist, hbm_used_gb=None):
     from paper_2212_13459_gb300 import native
     peaks = load_peaks()
     conv_tflops = tm["conv_flops"] / (tm["conv_ms"] / 1e3) / 1e12 if tm["conv_ms"] > 0 else None
@@ -331,6 +333,7 @@ def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E
         "clocks": clk,
         "gpu_launches": tm["launches"],
         "loss": E, "device_status": status,
+        "hbm_used_gb": hbm_used_gb,
         "kernel_ms_per_step": {"conv": tm["conv_ms"] / args.steps,
                                "gram": tm["gram_ms"] / args.steps,
                                "other": tm["other_ms"] / args.steps},

@@ -290,15 +290,13 @@ __global__ void __launch_bounds__(256) conv11_dgrad_scatter_kernel(
        q += (long long)gridDim.x * blockDim.x) {
     const int y = r.y0 + (int)(q / rw), x = r.x0 + (int)(q % rw);
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-#pragma unroll
-    for (int ky = 0; ky < 3; ky++)
-#pragma unroll
-      for (int kx = 0; kx < 3; kx++) {
+#pragma unroll 1
+    for (int k = 0; k < 9; k++) {
+        const int ky = k / 3, kx = k % 3;
         const int yy = y - ky + 1, xx = x - kx + 1;
         if (yy < 0 || yy >= Hb || xx < 0 || xx >= Wb) continue;
         const T *gp = g + (((size_t)b * Hb + yy) * Wb + xx) * 64;
-        const int k = ky * 3 + kx;
-#pragma unroll
+#pragma unroll 4
         for (int c8 = 0; c8 < 64; c8 += 8) {
           float gv[8];
           load8(gp + c8, gv);

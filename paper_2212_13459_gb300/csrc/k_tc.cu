@@ -253,6 +253,174 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+
+// ---- halo-reuse variant for the narrow layers ----------------------------------------------------
+// For Cout in {64, 128} and Cin in {64, 128} the whole weight tensor (<= 144 KB) stays in shared
+// memory for the life of the CTA, and each 64-channel K-block loads ONE activation box of
+// 18 rows x 16 pixels around a 16 x 8 output patch. The nine taps are nine descriptors into that
+// box, shifted by whole 128-byte pixel rows (the patch's 8-pixel rows are 2048 bytes apart), so
+// every input pixel crosses L2 -> shared memory once per K-block instead of nine times.
+constexpr int kHaloTH = 16, kHaloTW = 8, kHaloBoxW = 16, kHaloBoxH = kHaloTH + 2;
+constexpr uint32_t kHaloBoxBytes = kHaloBoxW * kHaloBoxH * 128;  // 36,864
+constexpr uint32_t kHaloSmemMax = 227 * 1024;
+
+template <int BN, int KB, int P2>
+struct HaloCfg {
+  static constexpr uint32_t TILE_B = BN * 128;                  // one (tap, K-block) weight tile
+  static constexpr uint32_t W_BYTES = (9 * KB + P2) * TILE_B;
+  static constexpr int STAGES_RAW = (int)((kHaloSmemMax - 1024 - W_BYTES) / kHaloBoxBytes);
+  static constexpr int STAGES = STAGES_RAW > 4 ? 4 : STAGES_RAW;
+  static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloBoxBytes;
+};
+
+template <int BN, int KB, int P2>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmA2,
+                        const __grid_constant__ CUtensorMap tmB2, const ConvArgs a,
+                        const TcGeom tg) {
+  using Cfg = HaloCfg<BN, KB, P2>;
+  constexpr int STAGES = Cfg::STAGES;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t IDESC = make_idesc(BN);
+  constexpr int KBT = KB + P2;   // K-blocks per tile
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], w_bar;
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const uint32_t w_base = smem_base, a_base = smem_base + Cfg::W_BYTES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&w_bar), 1);
+    for (int i = 0; i < 2; i++) {
+      mbar_init(smem_u32(&tfull_bar[i]), 1);
+      mbar_init(smem_u32(&tempty_bar[i]), 128);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // resident weights: tile (tap, cb) at w_base + (tap * KB + cb) * TILE_B, then R
+      const uint32_t wb = smem_u32(&w_bar);
+      mbar_expect_tx(wb, Cfg::W_BYTES);
+      for (int tap = 0; tap < 9; tap++)
+        for (int cb = 0; cb < KB; cb++)
+          tma_load_2d(w_base + (tap * KB + cb) * Cfg::TILE_B, &tmB, wb, tap * a.cin + cb * kBK, 0);
+      if (P2) tma_load_2d(w_base + 9 * KB * Cfg::TILE_B, &tmB2, wb, 0, 0);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
+        const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
+        const int b = t / (tg.tiles_x * tg.tiles_y);
+        for (int kb = 0; kb < KBT; kb++) {
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          mbar_expect_tx(fb, kHaloBoxBytes);
+          const uint32_t sa = a_base + stage * kHaloBoxBytes;
+          if (kb < KB)
+            tma_load_4d(sa, &tmA, fb, kb * kBK, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
+          else
+            tma_load_4d(sa, &tmA2, fb, 0, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(smem_u32(&w_bar), 0, &abort_flag, a.err);
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x, it++) {
+        const int acc = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+        bool first = true;
+        for (int kb = 0; kb < KBT; kb++) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = a_base + stage * kHaloBoxBytes;
+          const int tap0 = kb < KB ? 0 : 4, tap1 = kb < KB ? 9 : 5;   // phase 2: centre only
+          for (int tap = tap0; tap < tap1; tap++) {
+            const int dy = tap / 3, dx = tap % 3;   // box offsets 0..2 (= tap offset + 1)
+            // the swizzle is applied to absolute shared-memory address bits, so a start shifted by
+            // whole 128-byte rows keeps phase field 0 (the box itself starts 1024-aligned)
+            const uint32_t start = sa + (uint32_t)((dy * kHaloBoxW + dx) * 128);
+            const uint64_t da = sw128_desc_k(start, kHaloBoxW * 128, 0);
+            const uint32_t wt = kb < KB ? w_base + (tap * KB + kb) * Cfg::TILE_B
+                                        : w_base + 9 * KB * Cfg::TILE_B;
+            const uint64_t db = sw128_desc(wt);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; k++) {
+              mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, first ? 0u : 1u);
+              first = false;
+            }
+          }
+          mma_commit(smem_u32(&empty_bar[stage]));
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (ok) mma_commit(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int it = 0;
+    for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
+      const int acc = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      if (!mbar_wait(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      tc_fence_after();
+      const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
+      const int b = t / (tg.tiles_x * tg.tiles_y);
+      const int y = ty * kHaloTH + row / kHaloTW, x = tx * kHaloTW + row % kHaloTW;
+      const bool inb = y < a.Hb && x < a.Wb;
+      const BlockGeom g = a.geom[b];
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c, v);
+        if (inb) epilogue32(a, g, b, y, x, c, v);
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty_bar[acc]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
 // ---- host side -------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -336,6 +504,72 @@ void pick_patch(int H, int W, int &TH, int &TW) {
   }
 }
 
+template <int BN, int KB, int P2>
+cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
+                        const CUtensorMap &B2, const ConvArgs &a, cudaStream_t s) {
+  using Cfg = HaloCfg<BN, KB, P2>;
+  static_assert(Cfg::STAGES >= 2, "halo kernel needs two activation stages");
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  TcGeom tg{};
+  tg.TH = kHaloTH;
+  tg.TW = kHaloTW;
+  tg.tiles_x = (a.Wb + kHaloTW - 1) / kHaloTW;
+  tg.tiles_y = (a.Hb + kHaloTH - 1) / kHaloTH;
+  tg.n_tiles = 1;
+  tg.total = a.B * tg.tiles_x * tg.tiles_y;
+  const int grid = std::min(tg.total, g_num_sms);
+  conv_tc_halo_kernel<BN, KB, P2><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2, a, tg);
+  return cudaGetLastError();
+}
+
+// 4-D map of an activation with the halo box (64 ch, 16 px, 18 rows, 1)
+cudaError_t encode_act_halo(CUtensorMap *m, const void *ptr, int B, int H, int W, int C) {
+  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kHaloBoxW, (cuuint32_t)kHaloBoxH, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// the narrow layers whose weights fit in shared memory next to two activation stages
+bool halo_eligible(const ConvArgs &a) {
+  if (a.taps != 9) return false;
+  const int KB = a.cin / kBK;
+  if (a.cout == 64) return (KB == 1 && (a.k2 == 0 || a.k2 == 64)) || (KB == 2 && a.k2 == 0);
+  if (a.cout == 128) return KB == 1 && a.k2 == 0;
+  return false;
+}
+
+cudaError_t launch_conv_tc_halo(const ConvArgs &a, cudaStream_t s) {
+  CUtensorMap mA, mB, mA2, mB2;
+  cudaError_t e;
+  if ((e = encode_act_halo(&mA, a.A, a.B, a.Hb, a.Wb, a.cin)) != cudaSuccess) return e;
+  if ((e = encode_wt(&mB, a.Wt, a.cout, 9 * a.cin, a.cout)) != cudaSuccess) return e;
+  if (a.k2) {
+    if ((e = encode_act_halo(&mA2, a.A2, a.B, a.Hb, a.Wb, a.k2)) != cudaSuccess) return e;
+    if ((e = encode_wt(&mB2, a.W2, a.cout, a.k2, a.cout)) != cudaSuccess) return e;
+  } else {
+    mA2 = mA;
+    mB2 = mB;
+  }
+  const int KB = a.cin / kBK;
+  if (a.cout == 64 && KB == 1 && a.k2 == 0) return launch_halo<64, 1, 0>(mA, mB, mA2, mB2, a, s);
+  if (a.cout == 64 && KB == 1) return launch_halo<64, 1, 1>(mA, mB, mA2, mB2, a, s);
+  if (a.cout == 64 && KB == 2) return launch_halo<64, 2, 0>(mA, mB, mA2, mB2, a, s);
+  return launch_halo<128, 1, 0>(mA, mB, mA2, mB2, a, s);
+}
+
 }  // namespace
 
 bool tc_available() {
@@ -354,6 +588,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   if ((a.taps != 0 && a.taps != 9) || a.cout % 64 || (a.taps && a.cin % 64) || a.k2 % 64 ||
       (a.taps == 0 && a.k2 == 0))
     return cudaErrorInvalidValue;
+  if (halo_eligible(a)) return launch_conv_tc_halo(a, s);
   const int BN = a.cout >= 256 ? 256 : a.cout;
   TcGeom tg;
   pick_patch(a.Hb, a.Wb, tg.TH, tg.TW);

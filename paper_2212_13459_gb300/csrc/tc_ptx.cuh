@@ -125,6 +125,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// K-major 128-byte-swizzled descriptor with an explicit stride between 8-row groups and the
+// swizzle-pattern phase of the start address (bits 49-51).
+__device__ __forceinline__ uint64_t sw128_desc_k(uint32_t saddr, uint32_t sbo, uint32_t phase) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(phase & 7) << 49;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Shared-memory matrix descriptor, MN-major operand, 128-byte swizzle: an atom is 64 MN elements
 // (128 bytes) x 8 K rows; `lbo` = bytes between 64-element MN atoms, 8-row K groups 1024 apart.
 __device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) {

@@ -48,6 +48,9 @@ CASES = [  # B, H, W, cin, cout, k2, taps, mode
     (1, 33, 21, 512, 256, 256, 9, 1),
     (2, 7, 9, 0, 512, 512, 0, 1),
     (1, 64, 64, 64, 64, 64, 9, 1),
+    (2, 20, 33, 128, 64, 0, 9, 1),
+    (1, 40, 24, 64, 128, 0, 9, 0),
+    (3, 37, 29, 64, 64, 0, 9, 1),
 ]
 
 

@@ -112,6 +112,35 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
   for (int q = 0; q < 4; q++) st_bf16x8(out + 8 * q, v + 8 * q);
 }
 
+// ---- fused 2x2 max pooling in the forward epilogue ---------------------------------------------
+// The four pixels of a pooling window are rows (y, x), (y, x+1), (y+1, x), (y+1, x+1) of the
+// output patch. With 8- or 16-pixel-wide patches and 32 rows per epilogue warp they sit in one
+// warp at lanes l, l^1, l^TW, l^(TW+1): the max is two shuffles, and the window's top-left lane
+// writes the pooled value (the BF16 values, exactly as stored, so the result equals pooling the
+// stored activation). Outside the block's valid pooled region the pooled map is zero.
+__device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGeom &g, int b,
+                                                int y, int x, int n, int tw, float *v) {
+#pragma unroll
+  for (int j = 0; j < 32; j++) {
+    float f = __bfloat162float(__float2bfloat16_rn(v[j]));
+    f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, 1));
+    f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, tw));
+    v[j] = f;
+  }
+  if ((y & 1) || (x & 1) || y >= a.Hb || x >= a.Wb) return;
+  const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
+  const bool valid = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
+  __nv_bfloat16 *out =
+      reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + (((size_t)b * Hp + py) * Wp + px) * a.cout + n;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    float w8[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) w8[j] = valid ? v[8 * q + j] : 0.f;
+    st_bf16x8(out + 8 * q, w8);
+  }
+}
+
 // ---- the kernel -------------------------------------------------------------------------------------
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -240,6 +269,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
         if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
+        if (a.pool_out) {
+          if (!inb) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = 0.f;
+          }
+          pool_epilogue32(a, g, b, y, x, nt * BN + c, tg.TW, v);
+        }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
@@ -255,36 +291,39 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 
 // ---- halo-reuse variant for the narrow layers ----------------------------------------------------
-// For Cout in {64, 128} and Cin in {64, 128} the whole weight tensor (<= 144 KB) stays in shared
-// memory for the life of the CTA, and each 64-channel K-block loads ONE activation box of
-// 18 rows x 16 pixels around a 16 x 8 output patch. The nine taps are nine descriptors into that
-// box, shifted by whole 128-byte pixel rows (the patch's 8-pixel rows are 2048 bytes apart), so
-// every input pixel crosses L2 -> shared memory once per K-block instead of nine times.
-constexpr int kHaloTH = 16, kHaloTW = 8, kHaloBoxW = 16, kHaloBoxH = kHaloTH + 2;
-constexpr uint32_t kHaloBoxBytes = kHaloBoxW * kHaloBoxH * 128;  // 36,864
+// For the 64/128-channel layers the weights of one N slice (<= 160 KB) stay in shared memory for
+// the life of the CTA, and each 64-channel K-block loads ONE activation box of 18 rows x 10
+// pixels around a 16 x 8 output patch. The nine taps are nine descriptors into that box,
+// shifted by whole 128-byte pixel rows (the patch's 8-pixel rows are 1,280 bytes apart); the
+// hardware applies the 128-byte swizzle to absolute shared-memory address bits, so the shifted
+// starts read exactly what the TMA wrote. Every input pixel crosses L2 -> shared memory once
+// per K-block instead of nine times. Phase-2 K-blocks (the fused V R term) use the centre tap.
+constexpr int kHaloTH = 16, kHaloTW = 8, kHaloBoxW = kHaloTW + 2, kHaloBoxH = kHaloTH + 2;
+constexpr uint32_t kHaloBoxBytes = kHaloBoxW * kHaloBoxH * 128;        // 23,040
+constexpr uint32_t kHaloStage = (kHaloBoxBytes + 1023u) & ~1023u;      // 23,552
 constexpr uint32_t kHaloSmemMax = 227 * 1024;
 
-template <int BN, int KB, int P2>
+template <int BN, int KB, int P2KB, int NT>
 struct HaloCfg {
   static constexpr uint32_t TILE_B = BN * 128;                  // one (tap, K-block) weight tile
-  static constexpr uint32_t W_BYTES = (9 * KB + P2) * TILE_B;
-  static constexpr int STAGES_RAW = (int)((kHaloSmemMax - 1024 - W_BYTES) / kHaloBoxBytes);
+  static constexpr uint32_t W_BYTES = (9 * KB + P2KB) * TILE_B;
+  static constexpr int STAGES_RAW = (int)((kHaloSmemMax - 1024 - W_BYTES) / kHaloStage);
   static constexpr int STAGES = STAGES_RAW > 4 ? 4 : STAGES_RAW;
-  static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloBoxBytes;
+  static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloStage;
 };
 
-template <int BN, int KB, int P2>
+template <int BN, int KB, int P2KB, int NT>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmA2,
                         const __grid_constant__ CUtensorMap tmB2, const ConvArgs a,
                         const TcGeom tg) {
-  using Cfg = HaloCfg<BN, KB, P2>;
+  using Cfg = HaloCfg<BN, KB, P2KB, NT>;
   constexpr int STAGES = Cfg::STAGES;
   constexpr uint32_t TMEM_COLS = 2 * BN;
   constexpr uint32_t IDESC = make_idesc(BN);
-  constexpr int KBT = KB + P2;   // K-blocks per tile
+  constexpr int KBT = KB + P2KB;   // K-blocks per tile
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], w_bar;
@@ -295,6 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t w_base = smem_base, a_base = smem_base + Cfg::W_BYTES;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this CTA's N slice, and its share of the M tiles
+  const int nt = blockIdx.x % NT, m_first = blockIdx.x / NT, m_step = gridDim.x / NT;
+  const int m_total = tg.total;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
@@ -317,17 +359,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // resident weights: tile (tap, cb) at w_base + (tap * KB + cb) * TILE_B, then R
+      // resident weights of slice nt: tile (tap, cb) at w_base + (tap * KB + cb) * TILE_B, then
+      // the phase-2 tiles (R rows of the slice)
       const uint32_t wb = smem_u32(&w_bar);
       mbar_expect_tx(wb, Cfg::W_BYTES);
       for (int tap = 0; tap < 9; tap++)
         for (int cb = 0; cb < KB; cb++)
-          tma_load_2d(w_base + (tap * KB + cb) * Cfg::TILE_B, &tmB, wb, tap * a.cin + cb * kBK, 0);
-      if (P2) tma_load_2d(w_base + 9 * KB * Cfg::TILE_B, &tmB2, wb, 0, 0);
+          tma_load_2d(w_base + (tap * KB + cb) * Cfg::TILE_B, &tmB, wb, tap * a.cin + cb * kBK,
+                      nt * BN);
+      for (int cb = 0; cb < P2KB; cb++)
+        tma_load_2d(w_base + (9 * KB + cb) * Cfg::TILE_B, &tmB2, wb, cb * kBK, nt * BN);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
+      for (int t = m_first; t < m_total && ok; t += m_step) {
         const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
         const int b = t / (tg.tiles_x * tg.tiles_y);
         for (int kb = 0; kb < KBT; kb++) {
@@ -337,11 +382,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const uint32_t fb = smem_u32(&full_bar[stage]);
           mbar_expect_tx(fb, kHaloBoxBytes);
-          const uint32_t sa = a_base + stage * kHaloBoxBytes;
+          const uint32_t sa = a_base + stage * kHaloStage;
           if (kb < KB)
             tma_load_4d(sa, &tmA, fb, kb * kBK, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
           else
-            tma_load_4d(sa, &tmA2, fb, 0, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
+            tma_load_4d(sa, &tmA2, fb, (kb - KB) * kBK, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
@@ -352,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       int it = 0;
-      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x, it++) {
+      for (int t = m_first; t < m_total && ok; t += m_step, it++) {
         const int acc = it & 1;
         const uint32_t use = (uint32_t)(it >> 1);
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
@@ -365,16 +410,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t sa = a_base + stage * kHaloBoxBytes;
+          const uint32_t sa = a_base + stage * kHaloStage;
           const int tap0 = kb < KB ? 0 : 4, tap1 = kb < KB ? 9 : 5;   // phase 2: centre only
           for (int tap = tap0; tap < tap1; tap++) {
             const int dy = tap / 3, dx = tap % 3;   // box offsets 0..2 (= tap offset + 1)
-            // the swizzle is applied to absolute shared-memory address bits, so a start shifted by
-            // whole 128-byte rows keeps phase field 0 (the box itself starts 1024-aligned)
+            // shifted by whole 128-byte rows; the swizzle follows absolute address bits, so the
+            // phase field stays 0 (the box itself starts 1024-aligned)
             const uint32_t start = sa + (uint32_t)((dy * kHaloBoxW + dx) * 128);
             const uint64_t da = sw128_desc_k(start, kHaloBoxW * 128, 0);
             const uint32_t wt = kb < KB ? w_base + (tap * KB + kb) * Cfg::TILE_B
-                                        : w_base + 9 * KB * Cfg::TILE_B;
+                                        : w_base + (9 * KB + kb - KB) * Cfg::TILE_B;
             const uint64_t db = sw128_desc(wt);
 #pragma unroll
             for (int k = 0; k < kBK / 16; k++) {
@@ -392,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     const int row = q * 32 + lane;
     int it = 0;
-    for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
+    for (int t = m_first; t < m_total; t += m_step, it++) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
       if (!mbar_wait(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
@@ -407,7 +452,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < BN; c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
-        if (inb) epilogue32(a, g, b, y, x, c, v);
+        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
+        if (a.pool_out) {
+          if (!inb) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = 0.f;
+          }
+          pool_epilogue32(a, g, b, y, x, nt * BN + c, kHaloTW, v);
+        }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
@@ -493,25 +545,28 @@ cudaError_t launch_bn(const CUtensorMap &A, const CUtensorMap &B, const CUtensor
   return cudaGetLastError();
 }
 
-// output patch shape with the least padding over an H x W map (TH * TW = 128)
-void pick_patch(int H, int W, int &TH, int &TW) {
+// output patch shape with the least padding over an H x W map (TH * TW = 128); with fused
+// pooling only the shapes whose 2x2 windows stay inside one epilogue warp
+void pick_patch(int H, int W, int &TH, int &TW, bool pool) {
   static const int cand[5][2] = {{1, 128}, {2, 64}, {4, 32}, {8, 16}, {16, 8}};
   long long best = -1;
   for (auto &c : cand) {
+    if (pool && c[0] < 8) continue;
     const long long area = (long long)((H + c[0] - 1) / c[0]) * c[0] * ((W + c[1] - 1) / c[1]) *
                            c[1];
     if (best < 0 || area < best) { best = area; TH = c[0]; TW = c[1]; }
   }
 }
 
-template <int BN, int KB, int P2>
+template <int BN, int KB, int P2KB, int NT>
 cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, cudaStream_t s) {
-  using Cfg = HaloCfg<BN, KB, P2>;
+  using Cfg = HaloCfg<BN, KB, P2KB, NT>;
   static_assert(Cfg::STAGES >= 2, "halo kernel needs two activation stages");
+  static_assert(Cfg::SMEM <= kHaloSmemMax, "halo kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2KB, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
@@ -522,14 +577,15 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   tg.TW = kHaloTW;
   tg.tiles_x = (a.Wb + kHaloTW - 1) / kHaloTW;
   tg.tiles_y = (a.Hb + kHaloTH - 1) / kHaloTH;
-  tg.n_tiles = 1;
-  tg.total = a.B * tg.tiles_x * tg.tiles_y;
-  const int grid = std::min(tg.total, g_num_sms);
-  conv_tc_halo_kernel<BN, KB, P2><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2, a, tg);
+  tg.n_tiles = NT;
+  tg.total = a.B * tg.tiles_x * tg.tiles_y;   // M tiles; every slice covers all of them
+  int grid = std::min(tg.total * NT, g_num_sms);
+  grid = std::max(NT, grid / NT * NT);
+  conv_tc_halo_kernel<BN, KB, P2KB, NT><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2, a, tg);
   return cudaGetLastError();
 }
 
-// 4-D map of an activation with the halo box (64 ch, 16 px, 18 rows, 1)
+// 4-D map of an activation with the halo box (64 ch, 10 px, 18 rows, 1)
 cudaError_t encode_act_halo(CUtensorMap *m, const void *ptr, int B, int H, int W, int C) {
   cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
   cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
@@ -542,32 +598,38 @@ cudaError_t encode_act_halo(CUtensorMap *m, const void *ptr, int B, int H, int W
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// the narrow layers whose weights fit in shared memory next to two activation stages
-bool halo_eligible(const ConvArgs &a) {
-  if (a.taps != 9) return false;
-  const int KB = a.cin / kBK;
-  if (a.cout == 64) return (KB == 1 && (a.k2 == 0 || a.k2 == 64)) || (KB == 2 && a.k2 == 0);
-  if (a.cout == 128) return KB == 1 && a.k2 == 0;
+// (cin, cout, k2) of the narrow layers -> N slice width and counts; false if not a halo layer
+bool halo_shape(const ConvArgs &a, int *BN, int *KB, int *P2KB, int *NT) {
+  if (a.taps != 9 || a.cin % kBK || a.k2 % kBK) return false;
+  *KB = a.cin / kBK;
+  *P2KB = a.k2 / kBK;
+  if (a.cin == 64 && a.cout == 64 && a.k2 <= 64) { *BN = 64; *NT = 1; return true; }
+  if (a.cin == 64 && a.cout == 128 && a.k2 == 0) { *BN = 128; *NT = 1; return true; }
+  if (a.cin == 128 && a.cout == 64 && a.k2 == 0) { *BN = 64; *NT = 1; return true; }
+  if (a.cin == 128 && a.cout == 128 && (a.k2 == 0 || a.k2 == 128)) { *BN = 64; *NT = 2; return true; }
   return false;
 }
 
-cudaError_t launch_conv_tc_halo(const ConvArgs &a, cudaStream_t s) {
+cudaError_t launch_conv_tc_halo(const ConvArgs &a, int BN, int KB, int P2KB, int NT,
+                                cudaStream_t s) {
   CUtensorMap mA, mB, mA2, mB2;
   cudaError_t e;
   if ((e = encode_act_halo(&mA, a.A, a.B, a.Hb, a.Wb, a.cin)) != cudaSuccess) return e;
-  if ((e = encode_wt(&mB, a.Wt, a.cout, 9 * a.cin, a.cout)) != cudaSuccess) return e;
+  if ((e = encode_wt(&mB, a.Wt, a.cout, 9 * a.cin, BN)) != cudaSuccess) return e;
   if (a.k2) {
     if ((e = encode_act_halo(&mA2, a.A2, a.B, a.Hb, a.Wb, a.k2)) != cudaSuccess) return e;
-    if ((e = encode_wt(&mB2, a.W2, a.cout, a.k2, a.cout)) != cudaSuccess) return e;
+    if ((e = encode_wt(&mB2, a.W2, a.cout, a.k2, BN)) != cudaSuccess) return e;
   } else {
     mA2 = mA;
     mB2 = mB;
   }
-  const int KB = a.cin / kBK;
-  if (a.cout == 64 && KB == 1 && a.k2 == 0) return launch_halo<64, 1, 0>(mA, mB, mA2, mB2, a, s);
-  if (a.cout == 64 && KB == 1) return launch_halo<64, 1, 1>(mA, mB, mA2, mB2, a, s);
-  if (a.cout == 64 && KB == 2) return launch_halo<64, 2, 0>(mA, mB, mA2, mB2, a, s);
-  return launch_halo<128, 1, 0>(mA, mB, mA2, mB2, a, s);
+  if (BN == 64 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<64, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
+  if (BN == 64 && KB == 1 && P2KB == 1 && NT == 1) return launch_halo<64, 1, 1, 1>(mA, mB, mA2, mB2, a, s);
+  if (BN == 128 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<128, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
+  if (BN == 64 && KB == 2 && P2KB == 0 && NT == 1) return launch_halo<64, 2, 0, 1>(mA, mB, mA2, mB2, a, s);
+  if (BN == 64 && KB == 2 && P2KB == 0 && NT == 2) return launch_halo<64, 2, 0, 2>(mA, mB, mA2, mB2, a, s);
+  if (BN == 64 && KB == 2 && P2KB == 2 && NT == 2) return launch_halo<64, 2, 2, 2>(mA, mB, mA2, mB2, a, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -588,10 +650,11 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   if ((a.taps != 0 && a.taps != 9) || a.cout % 64 || (a.taps && a.cin % 64) || a.k2 % 64 ||
       (a.taps == 0 && a.k2 == 0))
     return cudaErrorInvalidValue;
-  if (halo_eligible(a)) return launch_conv_tc_halo(a, s);
+  int hBN, hKB, hP2, hNT;
+  if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
   const int BN = a.cout >= 256 ? 256 : a.cout;
   TcGeom tg;
-  pick_patch(a.Hb, a.Wb, tg.TH, tg.TW);
+  pick_patch(a.Hb, a.Wb, tg.TH, tg.TW, a.pool_out != nullptr);
   tg.tiles_x = (a.Wb + tg.TW - 1) / tg.TW;
   tg.tiles_y = (a.Hb + tg.TH - 1) / tg.TH;
   tg.n_tiles = a.cout / BN;

@@ -449,9 +449,12 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
     a.bias = ctx->d_bias[l];
     a.geom = geom;
     a.level = lv;
+    // the tensor-core epilogue writes the pooled map too
+    const bool fuse_pool = ctx->use_tc && kPoolAfter[l] && l < last_conv;
+    if (fuse_pool) a.pool_out = ws.pool[l];
     nst_status st = run_conv(ctx, a, s);
     if (st) return st;
-    if (kPoolAfter[l] && l < last_conv) {
+    if (kPoolAfter[l] && l < last_conv && !fuse_pool) {
       Timer tm(ctx, kTOther, s);
       ctx->launches++;
       launch_pool<T>((const T *)ws.act[l], (T *)ws.pool[l], bt.B, p.Hb >> (lv + 1),

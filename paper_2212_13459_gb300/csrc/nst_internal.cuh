@@ -74,6 +74,8 @@ struct ConvArgs {
   const BlockGeom *geom;  // [B]
   int level;
   unsigned *err;
+  void *pool_out;         // forward, tensor-core engine: also write the 2x2 max pool
+                          // [B][Hb/2][Wb/2][cout] (null = no fused pooling)
 };
 
 }  // namespace nst

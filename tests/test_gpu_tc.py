@@ -51,6 +51,8 @@ CASES = [  # B, H, W, cin, cout, k2, taps, mode
     (2, 20, 33, 128, 64, 0, 9, 1),
     (1, 40, 24, 64, 128, 0, 9, 0),
     (3, 37, 29, 64, 64, 0, 9, 1),
+    (2, 21, 30, 128, 128, 0, 9, 0),
+    (1, 33, 17, 128, 128, 128, 9, 1),
 ]
 
 

@@ -70,6 +70,17 @@ def lib():
             L.orc_table1_mse.argtypes = [dp, dp, ctypes.c_long, ctypes.c_double, dp, dp]
             L.orc_plan_1d.argtypes = [ctypes.c_int, ctypes.c_int, ip]
             L.orc_set_storage.argtypes = [ctypes.c_int]
+            L.orc_style_moments.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.orc_loss_grad_aug.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp,
+                                            dp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
+            L.orc_loss_grad_tiled_aug.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                                  dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
+                                                  dp, dp]
+            L.orc_table1_mean.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                          dp, dp]
+            L.orc_table1_std.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                         dp, dp]
             _lib = L
     return _lib
 
@@ -217,3 +228,74 @@ def plan_1d(L, k):
     rc = lib().orc_plan_1d(int(L), int(k), b)
     _check(rc)
     return list(b)
+
+
+STYLE_MOMENTS = sum(STYLE_CHANNELS)   # 1,472
+
+
+def split_vec(flat):
+    res, o = [], 0
+    for c in STYLE_CHANNELS:
+        res.append(flat[o:o + c].copy())
+        o += c
+    return res
+
+
+def style_moments(P, v):
+    """(mean, std) of the five style layers of v: lists of per-channel vectors (Eq. 5)."""
+    v = _img(v)
+    H, W = v.shape[1:]
+    m = np.zeros(STYLE_MOMENTS)
+    sd = np.zeros(STYLE_MOMENTS)
+    _check(lib().orc_style_moments(_p(P), _p(v), H, W, _p(m), _p(sd)))
+    return split_vec(m), split_vec(sd)
+
+
+def loss_grad_aug(P, x, content_t, style_G, style_mean, style_std, w_style, w_mean, w_std,
+                  lambda_c, want_grad=True, tiles=None, margins=(80, 160)):
+    """E(x) with the augmented style loss of Eq. 5 and dE/dx; untiled, or Algorithm 1 with
+    `tiles` blocks. Returns (E, grad or None, parts[6], grams[5])."""
+    x = _img(x)
+    H, W = x.shape[1:]
+    ct = np.ascontiguousarray(content_t, np.float64)
+    sg = join_grams(style_G)
+    sm = np.ascontiguousarray(np.concatenate(style_mean), np.float64)
+    ss = np.ascontiguousarray(np.concatenate(style_std), np.float64)
+    ws = np.ascontiguousarray(w_style, np.float64)
+    wm = np.ascontiguousarray(w_mean, np.float64)
+    wsd = np.ascontiguousarray(w_std, np.float64)
+    E = np.zeros(1)
+    parts = np.zeros(6)
+    grams = np.zeros(sg.size)
+    grad = np.zeros((3, H, W)) if want_grad else None
+    if tiles is None:
+        _check(lib().orc_loss_grad_aug(_p(P), _p(x), H, W, _p(ct), _p(sg), _p(sm), _p(ss),
+                                       _p(ws), _p(wm), _p(wsd), float(lambda_c), _p(E), _p(grad),
+                                       _p(parts), _p(grams)))
+    else:
+        _check(lib().orc_loss_grad_tiled_aug(_p(P), _p(x), H, W, _p(ct), _p(sg), _p(sm), _p(ss),
+                                             _p(ws), _p(wm), _p(wsd), float(lambda_c),
+                                             int(tiles[0]), int(tiles[1]), int(margins[0]),
+                                             int(margins[1]), _p(E), _p(grad), _p(parts),
+                                             _p(grams)))
+    return float(E[0]), grad, parts, split_grams(grams)
+
+
+def table1_mean(V, mu, w):
+    V = np.ascontiguousarray(V, np.float64)
+    npx, nc = V.shape
+    E = np.zeros(1)
+    g = np.zeros_like(V)
+    lib().orc_table1_mean(_p(V), npx, nc, _p(np.ascontiguousarray(mu, np.float64)), float(w),
+                          _p(E), _p(g))
+    return float(E[0]), g
+
+
+def table1_std(V, sigma, w):
+    V = np.ascontiguousarray(V, np.float64)
+    npx, nc = V.shape
+    E = np.zeros(1)
+    g = np.zeros_like(V)
+    lib().orc_table1_std(_p(V), npx, nc, _p(np.ascontiguousarray(sigma, np.float64)), float(w),
+                         _p(E), _p(g))
+    return float(E[0]), g

@@ -12,8 +12,12 @@
  *     conv4_4.
  *   - Gram matrices G^L = V^T V / n_p (Section 3.1, Eq. 4), Gram style loss (Eq. 3), content loss
  *     and transfer loss (Eq. 1-2).
- *   - Feature gradients of Table 1 (rows 1-2) and a hand-written reverse pass (ReLU mask, max-pool
+ *   - Feature gradients of Table 1 (rows 1-4) and a hand-written reverse pass (ReLU mask, max-pool
  *     routing, transposed 3x3 convolution) back to the image.
+ *   - The augmented style loss of Eq. 5 (Section 3.2): Gram term plus w'_L ||mean - mu||^2 and
+ *     w''_L ||std - sigma||^2, with std = (diag(G) - mean^2)^(1/2) (Algorithm 1, Step 1),
+ *     population statistics over the n_p feature pixels; a channel with std = 0 is constant, so
+ *     its std-term gradient (V - mean) * (...) / std is 0 (taken as 0, not 0/0).
  *   - Algorithm 1 (two passes over blocks extracted with a margin), literally, for the exactness
  *     and margin tests.
  *
@@ -332,8 +336,9 @@ static void gram_sum_rect(const double *V, int c, int h, int w, int y0, int y1, 
 
 /* Table 1, row 2: E = w ||G - Gref||_F^2 and dE/dV = w (4/np) V (G - Gref) (V is np x nc there;
  * here V is nc x npix and the gradient is written in the same layout). */
-static double gram_loss_grad(const double *V, int c, long npix, double np, const double *G,
-                             const double *Gref, double w, double *gV) {
+static double gram_loss_grad_ab(const double *V, int c, long npix, double np, const double *G,
+                                const double *Gref, double w, const double *beta,
+                                const double *alpha, double *gV) {
   double E = 0.0;
   for (long k = 0; k < (long)c * c; k++) {
     double d = G[k] - Gref[k];
@@ -344,13 +349,43 @@ static double gram_loss_grad(const double *V, int c, long npix, double np, const
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < c; j++) {
       double *gj = gV + (long)j * npix;
-      for (long p = 0; p < npix; p++) gj[p] = 0.0;
+      const double aj = alpha ? (g_storage ? (double)(float)alpha[j] : alpha[j]) : 0.0;
+      for (long p = 0; p < npix; p++) gj[p] = aj;
       for (int i = 0; i < c; i++) {
-        double dij = q((G[(long)i * c + j] - Gref[(long)i * c + j]) * (4.0 * w / np));
+        double rij = (G[(long)i * c + j] - Gref[(long)i * c + j]) * (4.0 * w / np);
+        if (beta && i == j) rij += beta[j];
+        const double dij = q(rij);
         const double *vi = V + (long)i * npix;
         for (long p = 0; p < npix; p++) gj[p] += vi[p] * dij;
       }
     }
+  }
+  return E;
+}
+
+static double gram_loss_grad(const double *V, int c, long npix, double np, const double *G,
+                             const double *Gref, double w, double *gV) {
+  return gram_loss_grad_ab(V, c, npix, np, G, Gref, w, NULL, NULL, gV);
+}
+
+/* Mean and std terms of Eq. 5 from the layer statistics: mean_j = S_j / n_p (S = channel sums),
+ * std_j = (G_jj - mean_j^2)^(1/2) (Algorithm 1, Step 1). Returns w' |mean - mu|^2 +
+ * w'' |std - sigma|^2 and the per-channel affine feature gradient of Table 1 rows 3-4:
+ * dE/dV_kj = alpha_j + beta_j V_kj with beta_j = w'' (2/n_p)(std_j - sigma_j)/std_j and
+ * alpha_j = w' (2/n_p)(mean_j - mu_j) - beta_j mean_j (beta_j = 0 when std_j = 0). */
+static double moment_terms(int c, double np, const double *G, const double *mean,
+                           const double *mu, const double *sigma, double wm, double ws,
+                           double *std_out, double *alpha, double *beta) {
+  double E = 0.0;
+  for (int j = 0; j < c; j++) {
+    const double m = mean[j];
+    const double var = G[(long)j * c + j] - m * m;
+    const double sd = var > 0.0 ? sqrt(var) : 0.0;
+    if (std_out) std_out[j] = sd;
+    E += wm * (m - mu[j]) * (m - mu[j]) + ws * (sd - sigma[j]) * (sd - sigma[j]);
+    const double b = sd > 0.0 ? ws * 2.0 / np * (sd - sigma[j]) / sd : 0.0;
+    if (beta) beta[j] = b;
+    if (alpha) alpha[j] = wm * 2.0 / np * (m - mu[j]) - b * m;
   }
   return E;
 }
@@ -390,6 +425,44 @@ void orc_table1_mse(const double *V, const double *Vref, long n, double lambda, 
   *E = lambda * e;
 }
 
+/* Table 1, row 3: E = w ||mean(V) - mu||^2, (dE/dV)_k = w (2/np) (mean(V) - mu) for every row k.
+ * V is np x nc row-major. */
+void orc_table1_mean(const double *V, int np, int nc, const double *mu, double w, double *E,
+                     double *gV) {
+  double e = 0.0;
+  for (int j = 0; j < nc; j++) {
+    double m = 0.0;
+    for (int k = 0; k < np; k++) m += V[(long)k * nc + j];
+    m /= np;
+    e += (m - mu[j]) * (m - mu[j]);
+    for (int k = 0; k < np; k++) gV[(long)k * nc + j] = w * 2.0 / np * (m - mu[j]);
+  }
+  *E = w * e;
+}
+
+/* Table 1, row 4: E = w ||std(V) - sigma||^2 (population std),
+ * (dE/dV)_kj = w (2/np) (V_kj - mean_j) (std_j - sigma_j) / std_j. */
+void orc_table1_std(const double *V, int np, int nc, const double *sigma, double w, double *E,
+                    double *gV) {
+  double e = 0.0;
+  for (int j = 0; j < nc; j++) {
+    double m = 0.0, m2 = 0.0;
+    for (int k = 0; k < np; k++) {
+      m += V[(long)k * nc + j];
+      m2 += V[(long)k * nc + j] * V[(long)k * nc + j];
+    }
+    m /= np;
+    m2 /= np;
+    double var = m2 - m * m;
+    double sd = var > 0.0 ? sqrt(var) : 0.0;
+    e += (sd - sigma[j]) * (sd - sigma[j]);
+    for (int k = 0; k < np; k++)
+      gV[(long)k * nc + j] =
+          sd > 0.0 ? w * 2.0 / np * (V[(long)k * nc + j] - m) * (sd - sigma[j]) / sd : 0.0;
+  }
+  *E = w * e;
+}
+
 /* ------------------------------------------------------------------------------------------- */
 /* untiled evaluation (the plain definition)                                                    */
 
@@ -425,17 +498,50 @@ int orc_style_grams(const double *params, const double *v, int H, int W, double 
   return ORC_OK;
 }
 
+/* spatial mean and std (population, std from diag(G) - mean^2) of the five style layers of v,
+ * concatenated (64 + 128 + 256 + 512 + 512 = 1,472 values each) */
+int orc_style_moments(const double *params, const double *v, int H, int W, double *mean_out,
+                      double *std_out) {
+  if (check_size(H, W)) return ORC_ERR_SHAPE;
+  acts_t A;
+  if (acts_alloc(&A, H, W)) return ORC_ERR_OOM;
+  vgg_forward(params, v, &A);
+  long o = 0;
+  for (int s = 0; s < NSTYLE; s++) {
+    int l = kStyleConv[s], c = kCout[l];
+    long npix = (long)A.h[l] * A.w[l];
+    double *G = (double *)malloc(sizeof(double) * (size_t)c * c);
+    gram_sum_rect(A.a[l], c, A.h[l], A.w[l], 0, A.h[l], 0, A.w[l], G);
+    for (long k = 0; k < (long)c * c; k++) G[k] /= (double)npix;
+    for (int j = 0; j < c; j++) {
+      double m = 0.0;
+      for (long p = 0; p < npix; p++) m += A.a[l][(long)j * npix + p];
+      mean_out[o + j] = m / (double)npix;
+    }
+    moment_terms(c, (double)npix, G, mean_out + o, mean_out + o, std_out + o, 0.0, 0.0,
+                 std_out + o, NULL, NULL);
+    free(G);
+    o += c;
+  }
+  acts_free(&A);
+  return ORC_OK;
+}
+
 /* content target V^{Lc}(u): 512 x floor(H/8) x floor(W/8) */
 int orc_content_target(const double *params, const double *u, int H, int W, double *out) {
   return orc_features(params, u, H, W, CONTENT_CONV, out);
 }
 
-/* E(x) = lambda_c ||V^Lc(x) - V^Lc(u)||^2 + sum_L w_L ||G^L(x) - G^L(v)||_F^2 (Eq. 1-3) and its
- * gradient with respect to x. parts[0..4] = style terms, parts[5] = content term (may be NULL);
- * grams_out receives G^L(x) (may be NULL); grad may be NULL (loss only). */
-int orc_loss_grad(const double *params, const double *x, int H, int W, const double *content_t,
-                  const double *style_G, const double *w_style, double lambda_c, double *E_out,
-                  double *grad, double *parts, double *grams_out) {
+/* E(x) = lambda_c ||V^Lc(x) - V^Lc(u)||^2 + sum_L E~^L_style (Eq. 1-3, 5) and its gradient with
+ * respect to x. E~^L_style = w_L ||G^L(x) - G^L(v)||_F^2 + w'_L ||mean - mu_L||^2 +
+ * w''_L ||std - sigma_L||^2; w_mean / w_std may be NULL (plain Gram loss, Eq. 3), then
+ * style_mean / style_std are unused. parts[0..4] = style terms per layer, parts[5] = content
+ * term (may be NULL); grams_out receives G^L(x) (may be NULL); grad may be NULL (loss only). */
+int orc_loss_grad_aug(const double *params, const double *x, int H, int W,
+                      const double *content_t, const double *style_G, const double *style_mean,
+                      const double *style_std, const double *w_style, const double *w_mean,
+                      const double *w_std, double lambda_c, double *E_out, double *grad,
+                      double *parts, double *grams_out) {
   if (check_size(H, W)) return ORC_ERR_SHAPE;
   acts_t A;
   if (acts_alloc(&A, H, W)) return ORC_ERR_OOM;
@@ -444,20 +550,41 @@ int orc_loss_grad(const double *params, const double *x, int H, int W, const dou
   double E = 0.0;
   const double *gref = style_G;
   double *gout = grams_out;
+  long mo = 0;
   int rc = ORC_OK;
+  const int aug = w_mean && w_std;
   for (int s = 0; s < NSTYLE; s++) {
     int l = kStyleConv[s], c = kCout[l], h = A.h[l], w = A.w[l];
     long npix = (long)h * w;
     double *G = (double *)malloc(sizeof(double) * (size_t)c * c);
     gram_sum_rect(A.a[l], c, h, w, 0, h, 0, w, G);
     for (long k = 0; k < (long)c * c; k++) G[k] /= (double)npix;
+    double *alpha = NULL, *beta = NULL;
+    double em = 0.0;
+    if (aug) {
+      double *mean = (double *)malloc(sizeof(double) * c);
+      alpha = (double *)malloc(sizeof(double) * c);
+      beta = (double *)malloc(sizeof(double) * c);
+      for (int j = 0; j < c; j++) {
+        double m = 0.0;
+        for (long p = 0; p < npix; p++) m += A.a[l][(long)j * npix + p];
+        mean[j] = m / (double)npix;
+      }
+      em = moment_terms(c, (double)npix, G, mean, style_mean + mo, style_std + mo, w_mean[s],
+                        w_std[s], NULL, alpha, beta);
+      free(mean);
+    }
     if (grad) fg[l] = (double *)malloc(sizeof(double) * (size_t)c * npix);
-    double e = gram_loss_grad(A.a[l], c, npix, (double)npix, G, gref, w_style[s], fg[l]);
+    double e = gram_loss_grad_ab(A.a[l], c, npix, (double)npix, G, gref, w_style[s], beta, alpha,
+                                 fg[l]) + em;
+    free(alpha);
+    free(beta);
     if (parts) parts[s] = e;
     E += e;
     if (gout) { memcpy(gout, G, sizeof(double) * (size_t)c * c); gout += (long)c * c; }
     free(G);
     gref += (long)c * c;
+    mo += c;
   }
   {
     int l = CONTENT_CONV;
@@ -478,6 +605,14 @@ int orc_loss_grad(const double *params, const double *x, int H, int W, const dou
   for (int l = 0; l < NCONV; l++) free(fg[l]);
   acts_free(&A);
   return rc;
+}
+
+/* the plain Gram loss (Eq. 1-3): orc_loss_grad_aug without the mean / std terms */
+int orc_loss_grad(const double *params, const double *x, int H, int W, const double *content_t,
+                  const double *style_G, const double *w_style, double lambda_c, double *E_out,
+                  double *grad, double *parts, double *grams_out) {
+  return orc_loss_grad_aug(params, x, H, W, content_t, style_G, NULL, NULL, w_style, NULL, NULL,
+                           lambda_c, E_out, grad, parts, grams_out);
 }
 
 /* ------------------------------------------------------------------------------------------- */
@@ -518,25 +653,34 @@ static void owned_range(int i0, int i1, int s, int n_glob, int *j0, int *j1) {
 }
 
 /* Algorithm 1 with a k_h x k_w partition, margin m1 in Step 1 and m2 in Step 2 (the paper uses
- * one margin for both). Same outputs as orc_loss_grad. */
-int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
-                        const double *content_t, const double *style_G, const double *w_style,
-                        double lambda_c, int k_h, int k_w, int m1, int m2, double *E_out,
-                        double *grad, double *parts, double *grams_out) {
+ * one margin for both). Step 1 adds each block's owned V V^T and channel sums; after it, mean and
+ * std = (diag(G) - mean^2)^(1/2). Same outputs as orc_loss_grad_aug. */
+int orc_loss_grad_tiled_aug(const double *params, const double *x, int H, int W,
+                            const double *content_t, const double *style_G,
+                            const double *style_mean, const double *style_std,
+                            const double *w_style, const double *w_mean, const double *w_std,
+                            double lambda_c, int k_h, int k_w, int m1, int m2, double *E_out,
+                            double *grad, double *parts, double *grams_out) {
+  const int aug = w_mean && w_std;
   if (check_size(H, W)) return ORC_ERR_SHAPE;
   /* margins are multiples of 16 so that every block's pooling grid is the image's */
   if (k_h < 1 || k_w < 1 || m1 < 0 || m2 < 0 || m1 % 16 || m2 % 16) return ORC_ERR_ARG;
   int *by = (int *)malloc(sizeof(int) * (k_h + 1)), *bx = (int *)malloc(sizeof(int) * (k_w + 1));
   if (plan_1d(H, k_h, by) || plan_1d(W, k_w, bx)) { free(by); free(bx); return ORC_ERR_SHAPE; }
   double *blk = (double *)malloc(sizeof(double) * 3 * (size_t)H * W);
-  double *Gs[NSTYLE];
-  long off[NSTYLE];
-  long tot = 0;
+  double *Gs[NSTYLE], *Ss[NSTYLE], *Al[NSTYLE], *Be[NSTYLE];
+  long off[NSTYLE], moff[NSTYLE];
+  long tot = 0, mtot = 0;
   for (int s = 0; s < NSTYLE; s++) {
     int c = kCout[kStyleConv[s]];
     Gs[s] = (double *)calloc((size_t)c * c, sizeof(double));
+    Ss[s] = (double *)calloc((size_t)c, sizeof(double));
+    Al[s] = (double *)calloc((size_t)c, sizeof(double));
+    Be[s] = (double *)calloc((size_t)c, sizeof(double));
     off[s] = tot;
+    moff[s] = mtot;
     tot += (long)c * c;
+    mtot += c;
   }
   int rc = ORC_OK;
 
@@ -558,9 +702,14 @@ int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
         owned_range(iy0, iy1, st, H / st, &jy0, &jy1);
         owned_range(ix0, ix1, st, W / st, &jx0, &jx1);
         double *S = (double *)calloc((size_t)c * c, sizeof(double));
-        gram_sum_rect(A.a[l], c, A.h[l], A.w[l], jy0 - ey0 / st, jy1 - ey0 / st, jx0 - ex0 / st,
-                      jx1 - ex0 / st, S);
+        const int ly0 = jy0 - ey0 / st, ly1 = jy1 - ey0 / st;
+        const int lx0 = jx0 - ex0 / st, lx1 = jx1 - ex0 / st;
+        gram_sum_rect(A.a[l], c, A.h[l], A.w[l], ly0, ly1, lx0, lx1, S);
         for (long k = 0; k < (long)c * c; k++) Gs[s][k] += S[k];
+        for (int ch = 0; ch < c; ch++)
+          for (int yy = ly0; yy < ly1; yy++)
+            for (int xx = lx0; xx < lx1; xx++)
+              Ss[s][ch] += A.a[l][((long)ch * A.h[l] + yy) * A.w[l] + xx];
         free(S);
       }
       acts_free(&A);
@@ -572,6 +721,11 @@ int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
       double np = (double)(H / st) * (double)(W / st);
       for (long k = 0; k < (long)c * c; k++) Gs[s][k] /= np;
       double e = gram_loss_grad(NULL, c, 0, np, Gs[s], style_G + off[s], w_style[s], NULL);
+      if (aug) {
+        for (int ch = 0; ch < c; ch++) Ss[s][ch] /= np;   /* channel sums -> mean */
+        e += moment_terms(c, np, Gs[s], Ss[s], style_mean + moff[s], style_std + moff[s],
+                          w_mean[s], w_std[s], NULL, Al[s], Be[s]);
+      }
       if (parts) parts[s] = e;
       E += e;
       if (grams_out) memcpy(grams_out + off[s], Gs[s], sizeof(double) * (size_t)c * c);
@@ -600,7 +754,8 @@ int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
         long npix = (long)A.h[l] * A.w[l];
         double np = (double)(H / st) * (double)(W / st);
         fg[l] = (double *)malloc(sizeof(double) * (size_t)c * npix + 8);
-        gram_loss_grad(A.a[l], c, npix, np, Gs[s], style_G + off[s], w_style[s], fg[l]);
+        gram_loss_grad_ab(A.a[l], c, npix, np, Gs[s], style_G + off[s], w_style[s],
+                          aug ? Be[s] : NULL, aug ? Al[s] : NULL, fg[l]);
       }
       /* content: loss over the owned pixels, gradient on the whole block (Table 1 row 1) */
       {
@@ -636,11 +791,24 @@ int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
     }
   if (parts) parts[NSTYLE] = Ec;
   *E_out = E + Ec;
-  for (int s = 0; s < NSTYLE; s++) free(Gs[s]);
+  for (int s = 0; s < NSTYLE; s++) {
+    free(Gs[s]);
+    free(Ss[s]);
+    free(Al[s]);
+    free(Be[s]);
+  }
   free(blk);
   free(by);
   free(bx);
   return rc;
+}
+
+int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
+                        const double *content_t, const double *style_G, const double *w_style,
+                        double lambda_c, int k_h, int k_w, int m1, int m2, double *E_out,
+                        double *grad, double *parts, double *grams_out) {
+  return orc_loss_grad_tiled_aug(params, x, H, W, content_t, style_G, NULL, NULL, w_style, NULL,
+                                 NULL, lambda_c, k_h, k_w, m1, m2, E_out, grad, parts, grams_out);
 }
 
 /* the oracle's block partition, exposed for tests */

@@ -54,7 +54,11 @@ enum { NST_CONV_AUTO = 0, NST_CONV_SIMT = 1, NST_CONV_TC = 2 };
  *               for both precisions; TC needs BF16).
  *   max_batch_tiles: tiles processed per launch (0 = all tiles of the pass, within
  *               workspace_limit_bytes).
- *   workspace_limit_bytes: device workspace cap for activations of a tile batch (0 = 64 GiB). */
+ *   workspace_limit_bytes: device workspace cap for activations of a tile batch (0 = 48 GiB).
+ *   w_mean[5], w_std[5]: w'_L and w''_L of the augmented style loss (Section 3.2, Eq. 5):
+ *               w'_L ||mean(V^L(x)) - mean(V^L(v))||^2 + w''_L ||std(V^L(x)) - std(V^L(v))||^2,
+ *               population statistics over the image, std = (diag(G) - mean^2)^(1/2)
+ *               (Algorithm 1, Step 1). 0 (the default) gives the plain Gram loss of Eq. 3. */
 typedef struct {
   float w_style[5];
   float lambda_c;
@@ -64,6 +68,8 @@ typedef struct {
   int conv_engine;
   int max_batch_tiles;
   long long workspace_limit_bytes;
+  float w_mean[5];
+  float w_std[5];
 } nst_config;
 
 /* Fill *cfg with the defaults: w_style = 0.2 each, lambda_c = 1e-3, 1 x 1 tiles, margins 80/160,
@@ -109,6 +115,11 @@ nst_status nst_get_stats(nst_ctx *ctx, double *parts_host, double *grams_host, v
 
 /* The stored style Gram matrices G^L(v) (same layout as grams_host above). Synchronizes. */
 nst_status nst_get_style_grams(nst_ctx *ctx, double *grams_host, void *stream);
+
+/* The stored style moments mean(V^L(v)) and std(V^L(v)) of the five style layers,
+ * concatenated (64 + 128 + 256 + 512 + 512 = 1,472 doubles each). Synchronizes. */
+nst_status nst_get_style_moments(nst_ctx *ctx, double *mean_host, double *std_host,
+                                 void *stream);
 
 /* Per-kernel-class device time accumulated since the last nst_set_timing() call (CUDA events
  * around every launch while timing is enabled), in milliseconds, and the FLOPs the convolution

@@ -76,6 +76,10 @@ __device__ __forceinline__ void conv_epilogue4(const ConvArgs &a, int b, int y, 
         for (int j = 0; j < 4; j++) v[j] += a.two_lambda * (ca[j] - ct[j]);
       }
     }
+    if (a.addvec && valid) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) v[j] += a.addvec[n + j];
+    }
     if (a.mask) {
       float m[4];
       load4(reinterpret_cast<const T *>(a.mask) + o, m);
@@ -583,19 +587,40 @@ void launch_gram_reduce(const float *part, int nchunks, int C, double *Gacc, cud
 // One CTA of 1024 threads per style layer; deterministic reduction.
 __global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs a) {
   __shared__ double red[1024];
+  __shared__ double beta_s[512];
   const StyleLayerArgs L = a.L[blockIdx.x];
   const long long n = (long long)L.C * L.C;
   const double inv = 1.0 / L.np, rs = 4.0 * L.w / L.np;
+  // mean / std terms (Eq. 5): per channel, from the channel sums and diag(G)
   double s = 0.0;
+  for (int j = threadIdx.x; j < L.C; j += blockDim.x) {
+    double b = 0.0;
+    if (L.S) {
+      const double m = L.S[j] * inv;
+      const double var = L.Gacc[(long long)j * L.C + j] * inv - m * m;
+      const double sd = var > 0.0 ? sqrt(var) : 0.0;
+      if (L.mean_out) L.mean_out[j] = m;
+      if (L.std_out) L.std_out[j] = sd;
+      if (L.mu) {
+        s += L.wm * (m - L.mu[j]) * (m - L.mu[j]) + L.ws * (sd - L.sigma[j]) * (sd - L.sigma[j]);
+        b = sd > 0.0 ? L.ws * 2.0 * inv * (sd - L.sigma[j]) / sd : 0.0;
+        if (L.alpha) L.alpha[j] = (float)(L.wm * 2.0 * inv * (L.S[j] * inv - L.mu[j]) - b * m);
+      }
+    }
+    beta_s[j] = b;
+  }
+  __syncthreads();
   for (long long e = threadIdx.x; e < n; e += blockDim.x) {
     const double G = L.Gacc[e] * inv;
     const double d = G - L.Ghat[e];
     L.Gout[e] = G;
-    s += d * d;
+    s += L.w * d * d;
+    const int i = (int)(e / L.C), j = (int)(e % L.C);
+    const double r = rs * d + (i == j ? beta_s[j] : 0.0);
     if (a.r_is_bf16)
-      reinterpret_cast<__nv_bfloat16 *>(L.R)[e] = __float2bfloat16_rn((float)(rs * d));
+      reinterpret_cast<__nv_bfloat16 *>(L.R)[e] = __float2bfloat16_rn((float)r);
     else
-      reinterpret_cast<float *>(L.R)[e] = (float)(rs * d);
+      reinterpret_cast<float *>(L.R)[e] = (float)r;
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -603,8 +628,55 @@ __global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs 
     if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.Eparts[blockIdx.x] = L.w * red[0];
+  if (threadIdx.x == 0) a.Eparts[blockIdx.x] = red[0];
 }
+
+// channel sums over owned pixels: partial[c][j] = sum over chunk c of V[p][j] (FP32 runs of 64
+// pixels added in FP64)
+template <typename T>
+__global__ void __launch_bounds__(256) chansum_partial_kernel(
+    const T *__restrict__ V, int Hb, int Wb, int C, const OwnRect *__restrict__ own,
+    const GramChunk *__restrict__ chunks, double *__restrict__ partial) {
+  const GramChunk ch = chunks[blockIdx.x];
+  const OwnRect r = own[ch.b];
+  const int rw = r.x1 - r.x0;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    double acc = 0.0;
+    for (int q0 = ch.p0; q0 < ch.p1; q0 += 64) {
+      float f = 0.f;
+      const int q1 = q0 + 64 < ch.p1 ? q0 + 64 : ch.p1;
+      for (int q = q0; q < q1; q++) {
+        const int y = r.y0 + q / rw, x = r.x0 + q % rw;
+        f += to_f(V[(((size_t)ch.b * Hb + y) * Wb + x) * C + j]);
+      }
+      acc += (double)f;
+    }
+    partial[(size_t)blockIdx.x * C + j] = acc;
+  }
+}
+
+__global__ void chansum_reduce_kernel(const double *__restrict__ partial, int nchunks, int C,
+                                      double *__restrict__ S) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += partial[(size_t)c * C + j];
+    S[j] += s;
+  }
+}
+
+template <typename T>
+void launch_chansum(const T *V, int Hb, int Wb, int C, const OwnRect *own,
+                    const GramChunk *chunks, int nchunks, double *partial, double *S,
+                    cudaStream_t s) {
+  if (nchunks <= 0) return;
+  chansum_partial_kernel<T><<<nchunks, 256, 0, s>>>(V, Hb, Wb, C, own, chunks, partial);
+  chansum_reduce_kernel<<<(C + 255) / 256, 256, 0, s>>>(partial, nchunks, C, S);
+}
+template void launch_chansum<float>(const float *, int, int, int, const OwnRect *,
+                                    const GramChunk *, int, double *, double *, cudaStream_t);
+template void launch_chansum<__nv_bfloat16>(const __nv_bfloat16 *, int, int, int,
+                                            const OwnRect *, const GramChunk *, int, double *,
+                                            double *, cudaStream_t);
 
 void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s) {
   style_finalize_kernel<<<kNStyle, 1024, 0, s>>>(a);

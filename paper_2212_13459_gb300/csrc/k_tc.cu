@@ -95,6 +95,10 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
           }
         }
       }
+      if (a.addvec) {
+#pragma unroll
+        for (int j = 0; j < 32; j++) v[j] += __ldg(a.addvec + n + j);
+      }
       if (a.mask) {
         const __nv_bfloat16 *mk = reinterpret_cast<const __nv_bfloat16 *>(a.mask) + o;
 #pragma unroll
@@ -606,7 +610,9 @@ bool halo_shape(const ConvArgs &a, int *BN, int *KB, int *P2KB, int *NT) {
   if (a.cin == 64 && a.cout == 64 && a.k2 <= 64) { *BN = 64; *NT = 1; return true; }
   if (a.cin == 64 && a.cout == 128 && a.k2 == 0) { *BN = 128; *NT = 1; return true; }
   if (a.cin == 128 && a.cout == 64 && a.k2 == 0) { *BN = 64; *NT = 1; return true; }
-  if (a.cin == 128 && a.cout == 128 && (a.k2 == 0 || a.k2 == 128)) { *BN = 64; *NT = 2; return true; }
+  // (the input gradient of conv2_2, k2 = 128, is faster on the main kernel: two N slices each
+  // re-read the boxes of both operands)
+  if (a.cin == 128 && a.cout == 128 && a.k2 == 0) { *BN = 64; *NT = 2; return true; }
   return false;
 }
 

@@ -31,6 +31,7 @@ using namespace nst;
 namespace {
 
 constexpr int kGramTotal = 64 * 64 + 128 * 128 + 256 * 256 + 512 * 512 + 512 * 512;  // 610304
+constexpr int kMomentTotal = 64 + 128 + 256 + 512 + 512;                               // 1472
 constexpr int kStyleC[kNStyle] = {64, 128, 256, 512, 512};
 constexpr long long kDefaultWorkspace = 48LL << 30;
 
@@ -49,6 +50,12 @@ long long gram_offset(int s) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int moment_offset(int s) {
+  int o = 0;
+  for (int i = 0; i < s; i++) o += kStyleC[i];
+  return o;
+}
 
 // ---- block partition ---------------------------------------------------------------------------
 // Interior boundaries on multiples of 16. Border blocks have no margin on their image side, so
@@ -117,6 +124,7 @@ struct PassPlan {
   GramChunk *d_chunks = nullptr;  // all chunks
   size_t gram_part_floats = 0;    // largest nchunks * npairs * 4096 (or tensor-core tiles)
   int max_content_chunks = 0;
+  size_t chansum_doubles = 0;     // largest nchunks * C (channel-sum partials)
   // tensor-core Gram: box shape per style layer, runs, and per-block owned-rectangle maps
   int tc_TH[kNStyle], tc_TW[kNStyle];
   GramTcChunk *d_tcchunks = nullptr;
@@ -160,6 +168,11 @@ struct nst_ctx {
   float *d_gpart = nullptr;
   size_t gpart_cap = 0;
   unsigned *d_err = nullptr;
+  // mean / std terms (Eq. 5)
+  bool aug = false;
+  double *d_sacc = nullptr, *d_mu = nullptr, *d_sigma = nullptr, *d_cspart = nullptr;
+  float *d_alpha = nullptr;
+  size_t cspart_cap = 0;
   // workspace (grow-only)
   void *d_ws = nullptr;
   size_t ws_cap = 0;
@@ -303,8 +316,10 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
           chunks.push_back({i - t0, (int)q, (int)std::min(n, q + ch), 0});
       }
       bt.nchunks[s] = (int)chunks.size() - bt.chunk_off[s];
-      if (s < kNStyle)
+      if (s < kNStyle) {
         p.gram_part_floats = std::max(p.gram_part_floats, (size_t)bt.nchunks[s] * npairs * 4096);
+        p.chansum_doubles = std::max(p.chansum_doubles, (size_t)bt.nchunks[s] * C);
+      }
       else
         p.max_content_chunks = std::max(p.max_content_chunks, bt.nchunks[s]);
     }
@@ -400,6 +415,12 @@ nst_status ensure_buffers(nst_ctx *ctx, const PassPlan &p, Workspace &ws) {
     CK(cudaMalloc(&ctx->d_gpart, p.gram_part_floats * sizeof(float)));
     ctx->gpart_cap = p.gram_part_floats;
   }
+  if (p.chansum_doubles > ctx->cspart_cap) {
+    if (ctx->d_cspart) CK(cudaFree(ctx->d_cspart));
+    ctx->d_cspart = nullptr;
+    CK(cudaMalloc(&ctx->d_cspart, sizeof(double) * p.chansum_doubles));
+    ctx->cspart_cap = p.chansum_doubles;
+  }
   if ((size_t)p.max_content_chunks > ctx->cpart_cap) {
     if (ctx->d_cpart) CK(cudaFree(ctx->d_cpart));
     ctx->d_cpart = nullptr;
@@ -490,8 +511,17 @@ nst_status ensure_gram_maps(nst_ctx *ctx, PassPlan &p, const Workspace &ws) {
 
 template <typename T>
 nst_status gram_batch(nst_ctx *ctx, PassPlan &p, const Batch &bt, const Workspace &ws,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool moments) {
   const int nt = (int)p.tiles.size();
+  if (moments)
+    for (int si = 0; si < kNStyle; si++) {
+      const int l = kStyleConv[si], lv = kLevel[l];
+      Timer tm(ctx, kTGram, s);
+      ctx->launches += 2;
+      launch_chansum<T>((const T *)ws.act[l], p.Hb >> lv, p.Wb >> lv, kCout[l],
+                        p.d_own + (size_t)si * nt + bt.t0, p.d_chunks + bt.chunk_off[si],
+                        bt.nchunks[si], ctx->d_cspart, ctx->d_sacc + moment_offset(si), s);
+    }
   if (ctx->use_tc) {
     nst_status st = ensure_gram_maps(ctx, p, ws);
     if (st) return st;
@@ -540,6 +570,7 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
     a.B = bt.B; a.Hb = p.Hb >> lv; a.Wb = p.Wb >> lv;
     a.cin = 0; a.cout = kCout[l]; a.taps = 0;
     a.k2 = kCout[l]; a.A2 = ws.act[l]; a.W2 = Rptr(4);
+    if (ctx->aug) a.addvec = ctx->d_alpha + moment_offset(4);
     a.out = ws.g[cur];
     a.mode = kEpiBackward;
     a.mask = ws.act[l];
@@ -562,7 +593,12 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
     if (!kPoolAfter[lp]) {
       a.mask = ws.act[lp];
       for (int si = 0; si < kNStyle; si++)
-        if (kStyleConv[si] == lp) { a.k2 = kCout[lp]; a.A2 = ws.act[lp]; a.W2 = Rptr(si); }
+        if (kStyleConv[si] == lp) {
+          a.k2 = kCout[lp];
+          a.A2 = ws.act[lp];
+          a.W2 = Rptr(si);
+          if (ctx->aug) a.addvec = ctx->d_alpha + moment_offset(si);
+        }
       if (lp == kContentConv) {
         a.cact = ws.act[lp];
         a.ctgt = ctx->d_ctgt;
@@ -596,7 +632,7 @@ enum PassKind { kPassStyleStats, kPassContentTarget };
 
 template <typename T>
 nst_status stats_pass(nst_ctx *ctx, const float *img, int H, int W, PassKind kind,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool moments = false) {
   PassPlan *p = nullptr;
   nst_status st = build_plan(ctx, H, W, ctx->cfg.margin1, &p);
   if (st) return st;
@@ -609,7 +645,7 @@ nst_status stats_pass(nst_ctx *ctx, const float *img, int H, int W, PassKind kin
     st = forward_batch<T>(ctx, *p, bt, ws, img, last, s);
     if (st) return st;
     if (kind == kPassStyleStats) {
-      st = gram_batch<T>(ctx, *p, bt, ws, s);
+      st = gram_batch<T>(ctx, *p, bt, ws, s, moments);
       if (st) return st;
     } else {
       ctx->launches++;
@@ -630,7 +666,8 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   launch_check_finite(x, 3LL * H * W, ctx->d_err, s);
   // Step 1: global statistics of x
   CK(cudaMemsetAsync(ctx->d_gacc, 0, sizeof(double) * kGramTotal, s));
-  nst_status st = stats_pass<T>(ctx, x, H, W, kPassStyleStats, s);
+  if (ctx->aug) CK(cudaMemsetAsync(ctx->d_sacc, 0, sizeof(double) * kMomentTotal, s));
+  nst_status st = stats_pass<T>(ctx, x, H, W, kPassStyleStats, s, ctx->aug);
   if (st) return st;
   StyleFinalizeArgs fa{};
   for (int si = 0; si < kNStyle; si++) {
@@ -642,6 +679,15 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
     fa.L[si].C = kStyleC[si];
     fa.L[si].np = (double)(H / stv) * (double)(W / stv);
     fa.L[si].w = ctx->cfg.w_style[si];
+    if (ctx->aug) {
+      const int mo = moment_offset(si);
+      fa.L[si].S = ctx->d_sacc + mo;
+      fa.L[si].mu = ctx->d_mu + mo;
+      fa.L[si].sigma = ctx->d_sigma + mo;
+      fa.L[si].wm = ctx->cfg.w_mean[si];
+      fa.L[si].ws = ctx->cfg.w_std[si];
+      fa.L[si].alpha = ctx->d_alpha + mo;
+    }
   }
   fa.Eparts = ctx->d_parts;
   fa.r_is_bf16 = ctx->bf16 ? 1 : 0;
@@ -810,8 +856,13 @@ nst_status nst_create(nst_ctx **out, const float *params, long long n_params,
       cudaMalloc(&ctx->d_R, ctx->esz * kGramTotal) != cudaSuccess ||
       cudaMalloc(&ctx->d_parts, sizeof(double) * 8) != cudaSuccess ||
       cudaMalloc(&ctx->d_loss, sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess)
+      cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_sacc, sizeof(double) * kMomentTotal) != cudaSuccess ||
+      cudaMalloc(&ctx->d_mu, sizeof(double) * kMomentTotal) != cudaSuccess ||
+      cudaMalloc(&ctx->d_sigma, sizeof(double) * kMomentTotal) != cudaSuccess ||
+      cudaMalloc(&ctx->d_alpha, sizeof(float) * kMomentTotal) != cudaSuccess)
     return bad(NST_ERR_OOM);
+  for (int i = 0; i < 5; i++) ctx->aug |= cfg->w_mean[i] != 0.f || cfg->w_std[i] != 0.f;
   cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   cudaMemset(ctx->d_parts, 0, sizeof(double) * 8);
   cudaMemset(ctx->d_gx, 0, sizeof(double) * kGramTotal);
@@ -834,6 +885,8 @@ nst_status nst_destroy(nst_ctx *ctx) {
   cudaFree(ctx->d_R); cudaFree(ctx->d_parts); cudaFree(ctx->d_loss); cudaFree(ctx->d_cpart);
   cudaFree(ctx->d_gpart); cudaFree(ctx->d_err); cudaFree(ctx->d_ws);
   cudaFree(ctx->d_xh); cudaFree(ctx->d_gh);
+  cudaFree(ctx->d_sacc); cudaFree(ctx->d_mu); cudaFree(ctx->d_sigma); cudaFree(ctx->d_alpha);
+  cudaFree(ctx->d_cspart);
   for (auto &kv : ctx->plans) {
     cudaFree(kv.second.d_geom);
     cudaFree(kv.second.d_own);
@@ -851,8 +904,9 @@ nst_status nst_style_targets(nst_ctx *ctx, const float *v, int Hv, int Wv, void 
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(ctx->d_gacc, 0, sizeof(double) * kGramTotal, s));
-  st = ctx->bf16 ? stats_pass<__nv_bfloat16>(ctx, v, Hv, Wv, kPassStyleStats, s)
-                 : stats_pass<float>(ctx, v, Hv, Wv, kPassStyleStats, s);
+  CK(cudaMemsetAsync(ctx->d_sacc, 0, sizeof(double) * kMomentTotal, s));
+  st = ctx->bf16 ? stats_pass<__nv_bfloat16>(ctx, v, Hv, Wv, kPassStyleStats, s, true)
+                 : stats_pass<float>(ctx, v, Hv, Wv, kPassStyleStats, s, true);
   if (st) return st;
   // G^L(v) = sum / n_p: the finaliser with w = 0 against a zero reference
   StyleFinalizeArgs fa{};
@@ -866,6 +920,10 @@ nst_status nst_style_targets(nst_ctx *ctx, const float *v, int Hv, int Wv, void 
     fa.L[si].C = kStyleC[si];
     fa.L[si].np = (double)(Hv / stv) * (double)(Wv / stv);
     fa.L[si].w = 0.0;
+    const int mo = moment_offset(si);
+    fa.L[si].S = ctx->d_sacc + mo;
+    fa.L[si].mean_out = ctx->d_mu + mo;
+    fa.L[si].std_out = ctx->d_sigma + mo;
   }
   fa.Eparts = ctx->d_parts;
   fa.r_is_bf16 = ctx->bf16 ? 1 : 0;
@@ -950,6 +1008,15 @@ nst_status nst_get_style_grams(nst_ctx *ctx, double *grams, void *stream) {
   if (!ctx->have_style) return fail(ctx, NST_ERR_STATE, "no style targets");
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   CK(cudaMemcpy(grams, ctx->d_ghat, sizeof(double) * kGramTotal, cudaMemcpyDeviceToHost));
+  return NST_OK;
+}
+
+nst_status nst_get_style_moments(nst_ctx *ctx, double *mean, double *sd, void *stream) {
+  if (!ctx || !mean || !sd) return fail(ctx, NST_ERR_INVALID_ARG, "null argument");
+  if (!ctx->have_style) return fail(ctx, NST_ERR_STATE, "no style targets");
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaMemcpy(mean, ctx->d_mu, sizeof(double) * kMomentTotal, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(sd, ctx->d_sigma, sizeof(double) * kMomentTotal, cudaMemcpyDeviceToHost));
   return NST_OK;
 }
 

@@ -76,6 +76,8 @@ struct ConvArgs {
   unsigned *err;
   void *pool_out;         // forward, tensor-core engine: also write the 2x2 max pool
                           // [B][Hb/2][Wb/2][cout] (null = no fused pooling)
+  const float *addvec;    // backward: per-channel term added at valid pixels before the gate
+                          // (alpha of the mean / std loss, Table 1 rows 3-4), or null
 };
 
 }  // namespace nst

@@ -15,10 +15,17 @@ struct StyleLayerArgs {
   const double *Gacc;  // sum over owned pixels of V V^T (FP64)
   const double *Ghat;  // G^L(v)
   double *Gout;        // G^L(x) = Gacc / np
-  void *R;             // (4 w / np)(G - Ghat), FP32 or BF16
+  void *R;             // (4 w / np)(G - Ghat) + diag(beta), FP32 or BF16
   int C;
   double np;
   double w;
+  // mean / std terms (Eq. 5), all optional: channel sums S, targets mu / sigma with weights
+  // wm / ws; alpha receives the per-channel gradient offset; mean_out / std_out the moments
+  const double *S;
+  const double *mu, *sigma;
+  double wm, ws;
+  float *alpha;
+  double *mean_out, *std_out;
 };
 struct StyleFinalizeArgs {
   StyleLayerArgs L[kNStyle];
@@ -49,6 +56,10 @@ void launch_gram_partial_flat(const T *V, long long npix, int C, long long chunk
                               float *part, cudaStream_t s);
 void launch_gram_reduce(const float *part, int nchunks, int C, double *Gacc, cudaStream_t s);
 void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s);
+template <typename T>
+void launch_chansum(const T *V, int Hb, int Wb, int C, const OwnRect *own,
+                    const GramChunk *chunks, int nchunks, double *partial, double *S,
+                    cudaStream_t s);
 template <typename T>
 void launch_content_loss(const T *V, int Hb, int Wb, const T *Vu, int Hc, int Wc,
                          const BlockGeom *geom, const OwnRect *own, const GramChunk *chunks,

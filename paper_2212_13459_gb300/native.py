@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
                 ("tiles_h", ctypes.c_int), ("tiles_w", ctypes.c_int),
                 ("margin1", ctypes.c_int), ("margin2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("conv_engine", ctypes.c_int),
-                ("max_batch_tiles", ctypes.c_int), ("workspace_limit_bytes", ctypes.c_longlong)]
+                ("max_batch_tiles", ctypes.c_int), ("workspace_limit_bytes", ctypes.c_longlong),
+                ("w_mean", ctypes.c_float * 5), ("w_std", ctypes.c_float * 5)]
 
 
 def lib():
@@ -64,6 +65,7 @@ def lib():
                 "nst_loss_grad_host": ([vp, fp, ip, ip, fp, dp, vp], ip),
                 "nst_get_stats": ([vp, dp, dp, vp], ip),
                 "nst_get_style_grams": ([vp, dp, vp], ip),
+                "nst_get_style_moments": ([vp, dp, dp, vp], ip),
                 "nst_get_timing": ([vp, dp, vp], ip),
                 "nst_set_timing": ([vp, ip], ip),
                 "nst_sync_status": ([vp, vp], ip),
@@ -114,9 +116,10 @@ def default_config(**kw) -> Config:
     c = Config()
     _check(lib().nst_config_default(ctypes.byref(c)))
     for k, v in kw.items():
-        if k == "w_style":
+        if k in ("w_style", "w_mean", "w_std"):
+            arr = getattr(c, k)
             for i in range(5):
-                c.w_style[i] = float(v[i])
+                arr[i] = float(v[i])
         else:
             setattr(c, k, v)
     return c
@@ -188,6 +191,19 @@ class Context:
         _check(lib().nst_get_style_grams(self.h, ctypes.c_void_p(g.ctypes.data),
                                          _stream(stream)), self.h)
         return split_grams(g)
+
+    def style_moments(self, stream=None):
+        m = np.zeros(sum(STYLE_CHANNELS))
+        sd = np.zeros(sum(STYLE_CHANNELS))
+        _check(lib().nst_get_style_moments(self.h, ctypes.c_void_p(m.ctypes.data),
+                                           ctypes.c_void_p(sd.ctypes.data), _stream(stream)),
+               self.h)
+        out_m, out_s, o = [], [], 0
+        for c in STYLE_CHANNELS:
+            out_m.append(m[o:o + c].copy())
+            out_s.append(sd[o:o + c].copy())
+            o += c
+        return out_m, out_s
 
     def set_timing(self, on=True):
         _check(lib().nst_set_timing(self.h, 1 if on else 0), self.h)

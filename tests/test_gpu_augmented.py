@@ -1,0 +1,100 @@
+"""GPU parity of the augmented style loss (Section 3.2, Eq. 5: Gram + mean + std terms, Table 1
+rows 3-4, std from diag(G) - mean^2 as in Algorithm 1) against the FP64 oracle."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2212_13459_gb300 import native, synth
+from tests._gpu import (LAMBDA_C, STYLE1_ONLY, TOL_BF16, TOL_BF16_FULL_GRAD, TOL_FP32, rel_l2,
+                        seeded)
+
+pytestmark = pytest.mark.gpu
+
+W_MEAN = (0.5, 0.3, 0.2, 0.1, 0.1)
+W_STD = (0.4, 0.3, 0.2, 0.2, 0.1)
+W_STYLE = (0.2,) * 5
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_aug(H, W, seed, storage, ws, wm, wsd, lam, tiles=None):
+    params, u, v, x = seeded(H, W, seed)
+    P = oracle.pack_params(params)
+    with oracle.storage(storage):
+        ct = oracle.content_target(P, u)
+        Gv = oracle.style_grams(P, v)
+        mv, sv = oracle.style_moments(P, v)
+        E, g, parts, Gx = oracle.loss_grad_aug(P, x, ct, Gv, mv, sv, ws, wm, wsd, lam)
+    return E, g, parts, mv, sv
+
+
+def gpu_aug(H, W, seed, ws, wm, wsd, lam, **cfg):
+    params, u, v, x = seeded(H, W, seed)
+    ctx = native.Context(synth.flat_params(params), w_style=ws, w_mean=wm, w_std=wsd,
+                         lambda_c=lam, **cfg)
+    ctx.style_targets(torch.from_numpy(v).cuda())
+    ctx.content_targets(torch.from_numpy(u).cuda())
+    xt = torch.from_numpy(x).cuda()
+    g = torch.empty_like(xt)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.loss_grad(xt, g, loss)
+    torch.cuda.synchronize()
+    parts, _ = ctx.stats(want_grams=False)
+    mv, sv = ctx.style_moments()
+    out = dict(E=loss.item(), g=g.cpu().numpy().astype(np.float64), parts=parts, mv=mv, sv=sv,
+               status=ctx.sync_status())
+    ctx.close()
+    return out
+
+
+FP32 = dict(precision=native.PREC_FP32, conv_engine=native.CONV_SIMT)
+TC = dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC)
+
+
+@pytest.mark.parametrize("case", [(64, 64, 0, 2), (100, 76, 2, 2)])
+def test_augmented_fp32(case):
+    H, W, seed, t = case
+    E, g, parts, mv, sv = oracle_aug(H, W, seed, "f32", W_STYLE, W_MEAN, W_STD, LAMBDA_C)
+    r = gpu_aug(H, W, seed, W_STYLE, W_MEAN, W_STD, LAMBDA_C, tiles_h=t, tiles_w=t, **FP32)
+    assert r["status"] == 0
+    for s in range(5):
+        assert rel_l2(r["mv"][s], mv[s]) <= TOL_FP32 and rel_l2(r["sv"][s], sv[s]) <= TOL_FP32
+    assert np.allclose(r["parts"], parts, rtol=TOL_FP32, atol=1e-12)
+    assert abs(r["E"] - E) <= TOL_FP32 * abs(E)
+    assert rel_l2(r["g"], g) <= TOL_FP32
+
+
+def test_augmented_bf16_tensor_cores():
+    E, g, parts, mv, sv = oracle_aug(128, 128, 1, "bf16", W_STYLE, W_MEAN, W_STD, LAMBDA_C)
+    r = gpu_aug(128, 128, 1, W_STYLE, W_MEAN, W_STD, LAMBDA_C, tiles_h=2, tiles_w=2, **TC)
+    assert r["status"] == 0
+    for s in range(5):
+        assert rel_l2(r["mv"][s], mv[s]) <= TOL_BF16 and rel_l2(r["sv"][s], sv[s]) <= TOL_BF16
+    assert abs(r["E"] - E) <= TOL_BF16 * abs(E)
+    assert rel_l2(r["g"], g) <= TOL_BF16_FULL_GRAD
+
+
+def test_augmented_relu1_1_terms_bf16_strict():
+    """Mean and std terms at ReLU1_1 only (no pooling decision on the gradient path)."""
+    wm, wsd = (0.5, 0, 0, 0, 0), (0.4, 0, 0, 0, 0)
+    E, g, parts, mv, sv = oracle_aug(96, 96, 3, "bf16", STYLE1_ONLY, wm, wsd, 0.0)
+    r = gpu_aug(96, 96, 3, STYLE1_ONLY, wm, wsd, 0.0, tiles_h=2, tiles_w=2, **TC)
+    assert abs(r["E"] - E) <= TOL_BF16 * abs(E)
+    assert rel_l2(r["g"], g) <= TOL_BF16
+
+
+def test_augmented_identity_exact_zero():
+    params, u, v, x = seeded(192, 160, 4)
+    for cfg in (FP32, TC):
+        ctx = native.Context(synth.flat_params(params), w_mean=W_MEAN, w_std=W_STD, tiles_h=2,
+                             tiles_w=2, **cfg)
+        ut = torch.from_numpy(u).cuda()
+        ctx.style_targets(ut)
+        ctx.content_targets(ut)
+        g = torch.full_like(ut, 7.0)
+        loss = torch.full((1,), 5.0, dtype=torch.float64, device="cuda")
+        ctx.loss_grad(ut, g, loss)
+        torch.cuda.synchronize()
+        assert loss.item() == 0.0 and torch.count_nonzero(g).item() == 0

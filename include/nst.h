@@ -161,6 +161,14 @@ nst_status nst_lbfgs_info(nst_lbfgs *st, int *pairs, long long *iters, void *str
 nst_status nst_upsample_init(const float *x_small_dev, int h, int w, float *x_dev, int H, int W,
                              void *stream);
 
+/* ---- multiscale downscaling (Algorithm 2, "downscale u and v by a factor 2^(n-s)") ---------
+ * Area averaging (adaptive average pooling) of x (3 x h x w, device) to out (3 x H x W, device),
+ * H <= h, W <= w: output pixel (Y, X) is the mean of the input rows [floor(Y h / H),
+ * ceil((Y+1) h / H)) and columns [floor(X w / W), ceil((X+1) w / W)); an integer factor gives
+ * the box mean. */
+nst_status nst_downscale(const float *x_dev, int h, int w, float *out_dev, int H, int W,
+                         void *stream);
+
 /* ---- single-layer convolution (unit-test entry of the convolution engines) -------------------
  * One 3x3 convolution layer of the trunk on NHWC tensors, as used inside nst_loss_grad:
  *   acc[b][y][x][n] = sum_{ky,kx,c} in[b][y+ky-1][x+kx-1][c] * w[n][ky*3+kx][c]      (taps = 9)

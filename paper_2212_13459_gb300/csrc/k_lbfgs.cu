@@ -239,4 +239,35 @@ void launch_bicubic(const float *x, int C, int h, int w, float *out, int H, int 
   bicubic_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(x, C, h, w, out, H, W);
 }
 
+// ---- area-average downscaling (adaptive average pooling) ---------------------------------------
+// out[c][Y][X] = mean of x[c][y][x] over y in [floor(Y h / H), ceil((Y+1) h / H)) and
+// x in [floor(X w / W), ceil((X+1) w / W)): the downscaling of (u, v) in Algorithm 2.
+__global__ void area_kernel(const float *__restrict__ x, int C, int h, int w,
+                            float *__restrict__ out, int H, int W) {
+  const long long n = (long long)C * H * W;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(i % W);
+    const int Y = (int)((i / W) % H);
+    const int c = (int)(i / ((long long)W * H));
+    const int y0 = (int)(((long long)Y * h) / H), y1 = (int)(((long long)(Y + 1) * h + H - 1) / H);
+    const int x0 = (int)(((long long)X * w) / W), x1 = (int)(((long long)(X + 1) * w + W - 1) / W);
+    const float *src = x + (size_t)c * h * w;
+    double acc = 0.0;
+    for (int y = y0; y < y1; y++) {
+      float row = 0.f;
+      for (int xx = x0; xx < x1; xx++) row += src[(size_t)y * w + xx];
+      acc += (double)row;
+    }
+    out[i] = (float)(acc / ((double)(y1 - y0) * (double)(x1 - x0)));
+  }
+}
+
+void launch_area(const float *x, int C, int h, int w, float *out, int H, int W, cudaStream_t s) {
+  long long n = (long long)C * H * W;
+  long long b = (n + 255) / 256;
+  int grid = (int)(b < 152 * 32 ? b : 152 * 32);
+  area_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(x, C, h, w, out, H, W);
+}
+
 }  // namespace nst

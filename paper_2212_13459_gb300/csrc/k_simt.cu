@@ -189,22 +189,14 @@ template void launch_conv_simt<__nv_bfloat16>(const ConvArgs &, cudaStream_t);
 // ---- conv1_1 forward from the planar image (block extraction fused) ----------------------------
 // out[b][y][x][c] = relu(b1[c] + sum W1[c][ci][ky][kx] * blk(ci, y+ky-1, x+kx-1)), where blk is the
 // block's extended rectangle of x and reads zero outside it (the block is a standalone image).
-// One thread computes all 64 channels of one pixel; every weight read is a float4 that all
-// threads of a warp share (one shared-memory transaction feeds 4 FMAs per thread).
+// One thread computes all 64 channels of one pixel. The 27 x 64 weights travel as a
+// __grid_constant__ kernel parameter: with the loops unrolled, every FMA takes its weight
+// straight from the constant bank, so no load instruction competes with the FMAs.
 template <typename T>
 __global__ void __launch_bounds__(128) conv11_fwd_kernel(const float *__restrict__ img, int H,
-                                                         int W, const float *__restrict__ w11,
-                                                         const float *__restrict__ b11,
+                                                         int W, const __grid_constant__ Conv11W cw,
                                                          const BlockGeom *__restrict__ geom,
                                                          int B, int Hb, int Wb, T *__restrict__ out) {
-  __shared__ __align__(16) float ws[27][64];
-  __shared__ __align__(16) float bs[64];
-  for (int i = threadIdx.x; i < 27 * 64; i += blockDim.x) {
-    const int co = i / 27, k = i % 27;  // k = ci*9 + ky*3 + kx
-    ws[k][co] = w11[i];
-  }
-  if (threadIdx.x < 64) bs[threadIdx.x] = b11[threadIdx.x];
-  __syncthreads();
   const long long npix = (long long)B * Hb * Wb;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
@@ -227,21 +219,12 @@ __global__ void __launch_bounds__(128) conv11_fwd_kernel(const float *__restrict
                 ok ? __ldg(img + ((size_t)ci * H + g.ey0 + yy) * W + g.ex0 + xx) : 0.f;
           }
 #pragma unroll
-      for (int c4 = 0; c4 < 16; c4++) {
-        const float4 b4 = *reinterpret_cast<const float4 *>(&bs[c4 * 4]);
-        acc[c4 * 4] = b4.x; acc[c4 * 4 + 1] = b4.y; acc[c4 * 4 + 2] = b4.z; acc[c4 * 4 + 3] = b4.w;
-      }
+      for (int c = 0; c < 64; c++) acc[c] = cw.b[c];
 #pragma unroll
       for (int k = 0; k < 27; k++) {
         const float v = in[k];
 #pragma unroll
-        for (int c4 = 0; c4 < 16; c4++) {
-          const float4 w4 = *reinterpret_cast<const float4 *>(&ws[k][c4 * 4]);
-          acc[c4 * 4] = fmaf(w4.x, v, acc[c4 * 4]);
-          acc[c4 * 4 + 1] = fmaf(w4.y, v, acc[c4 * 4 + 1]);
-          acc[c4 * 4 + 2] = fmaf(w4.z, v, acc[c4 * 4 + 2]);
-          acc[c4 * 4 + 3] = fmaf(w4.w, v, acc[c4 * 4 + 3]);
-        }
+        for (int c = 0; c < 64; c++) acc[c] = fmaf(cw.w[k][c], v, acc[c]);
       }
 #pragma unroll
       for (int c = 0; c < 64; c++) acc[c] = fmaxf(acc[c], 0.f);
@@ -256,17 +239,17 @@ __global__ void __launch_bounds__(128) conv11_fwd_kernel(const float *__restrict
 }
 
 template <typename T>
-void launch_conv11_fwd(const float *img, int H, int W, const float *w11, const float *b11,
-                       const BlockGeom *geom, int B, int Hb, int Wb, T *out, cudaStream_t s) {
+void launch_conv11_fwd(const float *img, int H, int W, const Conv11W &cw, const BlockGeom *geom,
+                       int B, int Hb, int Wb, T *out, cudaStream_t s) {
   long long npix = (long long)B * Hb * Wb;
   long long blocks = (npix + 127) / 128;
   int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-  conv11_fwd_kernel<T><<<grid, 128, 0, s>>>(img, H, W, w11, b11, geom, B, Hb, Wb, out);
+  conv11_fwd_kernel<T><<<grid, 128, 0, s>>>(img, H, W, cw, geom, B, Hb, Wb, out);
 }
-template void launch_conv11_fwd<float>(const float *, int, int, const float *, const float *,
+template void launch_conv11_fwd<float>(const float *, int, int, const Conv11W &,
                                        const BlockGeom *, int, int, int, float *, cudaStream_t);
-template void launch_conv11_fwd<__nv_bfloat16>(const float *, int, int, const float *,
-                                               const float *, const BlockGeom *, int, int, int,
+template void launch_conv11_fwd<__nv_bfloat16>(const float *, int, int, const Conv11W &,
+                                               const BlockGeom *, int, int, int,
                                                __nv_bfloat16 *, cudaStream_t);
 
 // ---- conv1_1 input gradient + scatter of the inner part into dE/dx --------------------------------
@@ -277,11 +260,14 @@ __global__ void __launch_bounds__(256) conv11_dgrad_scatter_kernel(
     const T *__restrict__ g, const float *__restrict__ w11, const BlockGeom *__restrict__ geom,
     const OwnRect *__restrict__ inner, int B, int Hb, int Wb, float *__restrict__ grad, int H,
     int W) {
-  // ws[k][co] = {W1[co][0][k], W1[co][1][k], W1[co][2][k], 0}: one float4 read per 3 FMAs
-  __shared__ __align__(16) float4 ws[9][64];
+  // Eight lanes per pixel, lane group cg holding channels 8cg..8cg+7: a warp reads four pixels'
+  // 128-byte channel vectors as 512 contiguous bytes. ws[k][cg][j] = {W1[co][0][k], W1[co][1][k],
+  // W1[co][2][k], 0} with co = 8cg + j, rows padded to 9 float4 so the 8 groups hit distinct banks.
+  __shared__ __align__(16) float4 ws[9][8][9];
   for (int i = threadIdx.x; i < 9 * 64; i += blockDim.x) {
     const int k = i / 64, co = i % 64;
-    ws[k][co] = make_float4(w11[co * 27 + k], w11[co * 27 + 9 + k], w11[co * 27 + 18 + k], 0.f);
+    ws[k][co / 8][co % 8] =
+        make_float4(w11[co * 27 + k], w11[co * 27 + 9 + k], w11[co * 27 + 18 + k], 0.f);
   }
   __syncthreads();
   const int b = blockIdx.y;
@@ -290,33 +276,42 @@ __global__ void __launch_bounds__(256) conv11_dgrad_scatter_kernel(
   const BlockGeom gm = geom[b];
   const int rw = r.x1 - r.x0, rh = r.y1 - r.y0;
   const long long n = (long long)rw * rh;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int y = r.y0 + (int)(q / rw), x = r.x0 + (int)(q % rw);
+  const int cg = threadIdx.x & 7;
+  const long long stride = (long long)gridDim.x * (blockDim.x >> 3);
+  // every lane of a warp runs the same number of iterations (the bound is per 4-pixel group)
+  for (long long q0 = (long long)blockIdx.x * (blockDim.x >> 3) + (threadIdx.x >> 5) * 4;
+       q0 < n; q0 += stride) {
+    const long long q = q0 + ((threadIdx.x & 31) >> 3);
+    const bool live = q < n;
+    const int y = live ? r.y0 + (int)(q / rw) : r.y0, x = live ? r.x0 + (int)(q % rw) : r.x0;
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-#pragma unroll 1
+#pragma unroll 3
     for (int k = 0; k < 9; k++) {
-        const int ky = k / 3, kx = k % 3;
-        const int yy = y - ky + 1, xx = x - kx + 1;
-        if (yy < 0 || yy >= Hb || xx < 0 || xx >= Wb) continue;
-        const T *gp = g + (((size_t)b * Hb + yy) * Wb + xx) * 64;
-#pragma unroll 4
-        for (int c8 = 0; c8 < 64; c8 += 8) {
-          float gv[8];
-          load8(gp + c8, gv);
+      const int yy = y - k / 3 + 1, xx = x - k % 3 + 1;
+      if (live && yy >= 0 && yy < Hb && xx >= 0 && xx < Wb) {
+        float gv[8];
+        load8(g + (((size_t)b * Hb + yy) * Wb + xx) * 64 + cg * 8, gv);
 #pragma unroll
-          for (int j = 0; j < 8; j++) {
-            const float4 w = ws[k][c8 + j];
-            d0 = fmaf(w.x, gv[j], d0);
-            d1 = fmaf(w.y, gv[j], d1);
-            d2 = fmaf(w.z, gv[j], d2);
-          }
+        for (int j = 0; j < 8; j++) {
+          const float4 w = ws[k][cg][j];
+          d0 = fmaf(w.x, gv[j], d0);
+          d1 = fmaf(w.y, gv[j], d1);
+          d2 = fmaf(w.z, gv[j], d2);
         }
       }
-    const size_t o = (size_t)(gm.ey0 + y) * W + gm.ex0 + x;
-    grad[o] = d0;
-    grad[(size_t)H * W + o] = d1;
-    grad[2 * (size_t)H * W + o] = d2;
+    }
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+      d0 += __shfl_xor_sync(0xffffffffu, d0, m);
+      d1 += __shfl_xor_sync(0xffffffffu, d1, m);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, m);
+    }
+    if (live && cg == 0) {
+      const size_t o = (size_t)(gm.ey0 + y) * W + gm.ex0 + x;
+      grad[o] = d0;
+      grad[(size_t)H * W + o] = d1;
+      grad[2 * (size_t)H * W + o] = d2;
+    }
   }
 }
 
@@ -324,8 +319,8 @@ template <typename T>
 void launch_conv11_dgrad_scatter(const T *g, const float *w11, const BlockGeom *geom,
                                  const OwnRect *inner, int B, int Hb, int Wb, float *grad, int H,
                                  int W, int max_inner_px, cudaStream_t s) {
-  int gx = (max_inner_px + 255) / 256;
-  if (gx > 1024) gx = 1024;
+  int gx = (max_inner_px + 31) / 32;   // 32 pixels per 256-thread CTA pass
+  if (gx > 2048) gx = 2048;
   if (gx < 1) gx = 1;
   dim3 grid(gx, B);
   conv11_dgrad_scatter_kernel<T><<<grid, 256, 0, s>>>(g, w11, geom, inner, B, Hb, Wb, grad, H, W);
@@ -596,15 +591,17 @@ __global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs 
   for (int j = threadIdx.x; j < L.C; j += blockDim.x) {
     double b = 0.0;
     if (L.S) {
-      const double m = L.S[j] * inv;
-      const double var = L.Gacc[(long long)j * L.C + j] * inv - m * m;
+      // rounded products (no contraction into an FMA), so the loss pass reproduces the target
+      // pass's mean bit for bit when x = v
+      const double m = __dmul_rn(L.S[j], inv);
+      const double var = __dmul_rn(L.Gacc[(long long)j * L.C + j], inv) - __dmul_rn(m, m);
       const double sd = var > 0.0 ? sqrt(var) : 0.0;
       if (L.mean_out) L.mean_out[j] = m;
       if (L.std_out) L.std_out[j] = sd;
       if (L.mu) {
         s += L.wm * (m - L.mu[j]) * (m - L.mu[j]) + L.ws * (sd - L.sigma[j]) * (sd - L.sigma[j]);
         b = sd > 0.0 ? L.ws * 2.0 * inv * (sd - L.sigma[j]) / sd : 0.0;
-        if (L.alpha) L.alpha[j] = (float)(L.wm * 2.0 * inv * (L.S[j] * inv - L.mu[j]) - b * m);
+        if (L.alpha) L.alpha[j] = (float)(L.wm * 2.0 * inv * (m - L.mu[j]) - b * m);
       }
     }
     beta_s[j] = b;

@@ -12,7 +12,7 @@
 // NHWC activation at the tap's offset: out-of-range coordinates read as zero, which is exactly
 // the convolution's zero padding. Both operands use the 128-byte swizzled K-major layout.
 //
-// Roles (192 threads): warp 0 issues TMA, warp 1 owns TMEM and issues tcgen05.mma, warps 2..5
+// Roles (320 threads): warp 0 issues TMA, warp 1 owns TMEM and issues tcgen05.mma, warps 2..9
 // drain the accumulator (tcgen05.ld), apply the epilogue and store BF16. Two TMEM accumulators
 // let the epilogue of one tile overlap the main loop of the next. Every mbarrier wait is bounded:
 // on timeout the kernel latches kErrTimeout in the status word and returns.
@@ -29,7 +29,10 @@ namespace {
 
 using namespace nst::tc;
 
-constexpr int kThreads = 192;
+// warp 0: TMA, warp 1: TMEM + MMA, warps 2..9: epilogue (two warps per TMEM lane quarter, each
+// draining half of the accumulator's columns)
+constexpr int kThreads = 320;
+constexpr int kEpiThreads = 256;
 constexpr int kBK = 64;                           // channels per K-block (128 bytes of BF16)
 
 struct TcGeom {
@@ -72,8 +75,15 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
   const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
   const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
   if (a.mode == kEpiForward) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + n);
 #pragma unroll
-    for (int j = 0; j < 32; j++) v[j] = valid ? fmaxf(v[j] + __ldg(a.bias + n + j), 0.f) : 0.f;
+    for (int q = 0; q < 8; q++) {
+      const float4 bb = __ldg(b4 + q);
+      v[4 * q] = valid ? fmaxf(v[4 * q] + bb.x, 0.f) : 0.f;
+      v[4 * q + 1] = valid ? fmaxf(v[4 * q + 1] + bb.y, 0.f) : 0.f;
+      v[4 * q + 2] = valid ? fmaxf(v[4 * q + 2] + bb.z, 0.f) : 0.f;
+      v[4 * q + 3] = valid ? fmaxf(v[4 * q + 3] + bb.w, 0.f) : 0.f;
+    }
   } else {
     if (!valid) {
 #pragma unroll
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; i++) {
       mbar_init(smem_u32(&tfull_bar[i]), 1);
-      mbar_init(smem_u32(&tempty_bar[i]), 128);
+      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -254,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
     const int q = warp & 3;           // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2; // which half of the accumulator columns it drains
     const int row = q * 32 + lane;    // M row = pixel of the patch
     int it = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
+      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
         if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(smem_u32(&w_bar), 1);
     for (int i = 0; i < 2; i++) {
       mbar_init(smem_u32(&tfull_bar[i]), 1);
-      mbar_init(smem_u32(&tempty_bar[i]), 128);
+      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -439,6 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = q * 32 + lane;
     int it = 0;
     for (int t = m_first; t < m_total; t += m_step, it++) {
@@ -453,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
+      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
         if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);

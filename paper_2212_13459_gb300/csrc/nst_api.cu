@@ -150,6 +150,7 @@ struct nst_ctx {
   std::string err;
   // weights
   float *d_w11 = nullptr;       // conv1_1 [64][3][3][3]
+  Conv11W h_c11{};              // conv1_1 weights / bias as a kernel parameter
   float *d_bias[kNConv] = {};
   void *d_wf[kNConv] = {};      // [cout][9][cin]
   void *d_wd[kNConv] = {};      // [cin][9][cout], taps flipped
@@ -455,8 +456,7 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
   {
     Timer tm(ctx, kTOther, s);
     ctx->launches++;
-    launch_conv11_fwd<T>(img, p.H, p.W, ctx->d_w11, ctx->d_bias[0], geom, bt.B, p.Hb, p.Wb,
-                         (T *)ws.act[0], s);
+    launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);
   }
   for (int l = 1; l <= last_conv; l++) {
     const int lv = kLevel[l];
@@ -822,6 +822,10 @@ nst_status nst_create(nst_ctx **out, const float *params, long long n_params,
     if (cudaMalloc(&ctx->d_bias[l], sizeof(float) * co) != cudaSuccess) return bad(NST_ERR_OOM);
     cudaMemcpy(ctx->d_bias[l], bl, sizeof(float) * co, cudaMemcpyHostToDevice);
     if (l == 0) {
+      for (int o = 0; o < co; o++) {
+        for (int k = 0; k < 27; k++) ctx->h_c11.w[k][o] = Wl[(size_t)o * 27 + k];
+        ctx->h_c11.b[o] = bl[o];
+      }
       if (cudaMalloc(&ctx->d_w11, sizeof(float) * co * ci * 9) != cudaSuccess)
         return bad(NST_ERR_OOM);
       cudaMemcpy(ctx->d_w11, Wl, sizeof(float) * co * ci * 9, cudaMemcpyHostToDevice);

@@ -138,4 +138,10 @@ nst_status nst_upsample_init(const float *xs, int h, int w, float *x, int H, int
   return cudaGetLastError() == cudaSuccess ? NST_OK : NST_ERR_CUDA;
 }
 
+nst_status nst_downscale(const float *x, int h, int w, float *out, int H, int W, void *stream) {
+  if (!x || !out || h < 1 || w < 1 || H < 1 || W < 1 || H > h || W > w) return NST_ERR_INVALID_ARG;
+  launch_area(x, 3, h, w, out, H, W, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? NST_OK : NST_ERR_CUDA;
+}
+
 }  // extern "C"

@@ -33,11 +33,18 @@ struct StyleFinalizeArgs {
   int r_is_bf16;
 };
 
+// conv1_1 weights and biases as one kernel parameter (7,168 bytes): w[k][c] = W1[c][k] with
+// k = ci * 9 + ky * 3 + kx
+struct Conv11W {
+  float w[27][64];
+  float b[64];
+};
+
 // k_simt.cu
 template <typename T> void launch_conv_simt(const ConvArgs &a, cudaStream_t s);
 template <typename T>
-void launch_conv11_fwd(const float *img, int H, int W, const float *w11, const float *b11,
-                       const BlockGeom *geom, int B, int Hb, int Wb, T *out, cudaStream_t s);
+void launch_conv11_fwd(const float *img, int H, int W, const Conv11W &cw, const BlockGeom *geom,
+                       int B, int Hb, int Wb, T *out, cudaStream_t s);
 template <typename T>
 void launch_conv11_dgrad_scatter(const T *g, const float *w11, const BlockGeom *geom,
                                  const OwnRect *inner, int B, int Hb, int Wb, float *grad, int H,
@@ -98,5 +105,6 @@ cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStr
 // k_lbfgs.cu (L-BFGS launchers are declared in nst_lbfgs_dev.h)
 void launch_bicubic(const float *x, int C, int h, int w, float *out, int H, int W,
                     cudaStream_t s);
+void launch_area(const float *x, int C, int h, int w, float *out, int H, int W, cudaStream_t s);
 
 }  // namespace nst

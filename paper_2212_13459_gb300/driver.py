@@ -66,19 +66,32 @@ def resample(img, H, W):
     return out
 
 
+def downscale(img, H, W):
+    """Area-average downscaling of a 3 x h x w device image to 3 x H x W (nst_downscale)."""
+    out = torch.empty((3, H, W), device=img.device, dtype=torch.float32)
+    native.downscale(img.contiguous(), out)
+    return out
+
+
+def scaled(n, f):
+    """n / f rounded half up (4226 / 4 -> 1057), at least 16 px."""
+    return max(16, int(n / f + 0.5))
+
+
 def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callback=None,
                **cfg):
-    """Algorithm 2: for s = 1..n, downscale (u, v) by 2^(n-s); x = u at the first scale, else
-    the previous x upscaled by 2; then L-BFGS with localized gradients (history 100 at the first
-    scale, 10 afterwards). tiles_for(H, W) -> (k_h, k_w) picks the block grid of a scale."""
+    """Algorithm 2: for s = 1..n, downscale (u, v) by 2^(n-s) (area averaging, sizes rounded);
+    x = u at the first scale, else the previous x upscaled by 2 (bicubic); then L-BFGS with
+    localized gradients (history 100 at the first scale, 10 afterwards).
+    tiles_for(H, W) -> (k_h, k_w) picks the block grid of a scale."""
     schedule = schedule or spst_schedule(n_scales)
     x = None
     for s in range(1, n_scales + 1):
         f = 2 ** (n_scales - s)
-        Hs, Ws = max(16, round(u.shape[1] / f)), max(16, round(u.shape[2] / f))
-        Hv, Wv = max(16, round(v.shape[1] / f)), max(16, round(v.shape[2] / f))
-        us = u if f == 1 else resample(u, Hs, Ws)
-        vs = v if f == 1 else resample(v, Hv, Wv)
+        Hs, Ws = scaled(u.shape[1], f), scaled(u.shape[2], f)
+        Hv, Wv = scaled(v.shape[1], f), scaled(v.shape[2], f)
+        us = u if f == 1 else downscale(u, Hs, Ws)
+        vs = v if f == 1 else downscale(v, Hv, Wv)
         x = us.clone() if x is None else resample(x, Hs, Ws)
         kh, kw = tiles_for(Hs, Ws) if tiles_for else (1, 1)
         ctx = native.Context(params_flat, tiles_h=kh, tiles_w=kw, **cfg)
@@ -88,3 +101,18 @@ def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callb
                        callback=(lambda k, l, s=s: callback(s, k, l)) if callback else None)
         ctx.close()
     return x
+
+
+def texture_synthesis(params_flat, v, H, W, n_scales, schedule=None, seed=0, tiles_for=None,
+                      callback=None, **cfg):
+    """Texture synthesis (Section 6.2): the multiscale loop with no content term (lambda_c = 0),
+    starting from white noise at the coarsest scale; the output is H x W."""
+    g = torch.Generator(device=v.device).manual_seed(seed)
+    f = 2 ** (n_scales - 1)
+    noise = torch.rand((3, scaled(H, f), scaled(W, f)), device=v.device, generator=g)
+    # the content image only fixes the sizes (its term has weight 0); noise at every scale
+    u = resample(noise, H, W)
+    cfg = dict(cfg)
+    cfg["lambda_c"] = 0.0
+    return multiscale(params_flat, u, v, n_scales, schedule=schedule, tiles_for=tiles_for,
+                      callback=callback, **cfg)

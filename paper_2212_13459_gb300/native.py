@@ -77,6 +77,7 @@ def lib():
                 "nst_lbfgs_info": ([vp, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_longlong), vp], ip),
                 "nst_upsample_init": ([fp, ip, ip, fp, ip, ip, vp], ip),
+                "nst_downscale": ([fp, ip, ip, fp, ip, ip, vp], ip),
                 "nst_version": ([], ctypes.c_char_p),
                 "nst_conv3x3": ([ip, ip, ip, ip, ip, ip, ip, ip, vp, vp, ip, vp, vp, vp, ip, vp,
                                  vp, vp, vp], ip),
@@ -257,6 +258,11 @@ class LBFGS:
             self.close()
         except Exception:
             pass
+
+
+def downscale(x, out, stream=None):
+    _check(lib().nst_downscale(_ptr(x), x.shape[1], x.shape[2], _ptr(out), out.shape[1],
+                               out.shape[2], _stream(stream)))
 
 
 def upsample_init(x_small, out, stream=None):

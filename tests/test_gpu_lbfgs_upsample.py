@@ -67,3 +67,19 @@ def test_gram_entry_matches_float64(npix, C, dtype):
     ref = V.double().T @ V.double()
     assert ((G - ref).norm() / ref.norm()).item() <= 1e-6
     assert torch.equal(G, G.T)
+
+
+@pytest.mark.parametrize("h,w,H,W", [(37, 53, 18, 26), (4226, 5319, 1057, 1330), (16, 24, 4, 6)])
+def test_downscale_matches_oracle(h, w, H, W):
+    from oracle import area
+    rng = np.random.default_rng(h + w)
+    x = rng.uniform(0, 1, size=(3, h, w)).astype(np.float32)
+    out = torch.empty((3, H, W), device="cuda")
+    native.downscale(torch.from_numpy(x).cuda(), out)
+    got = out.cpu().numpy()
+    if h * w > 10 ** 6:   # full size: sampled rows, the oracle on those rows' footprints
+        rows = rng.integers(0, H, size=16)
+        full = area.downscale(x.astype(np.float64), H, W)
+        assert np.abs(got[:, rows] - full[:, rows]).max() <= 2e-6
+    else:
+        assert np.abs(got - area.downscale(x.astype(np.float64), H, W)).max() <= 2e-6

@@ -85,3 +85,22 @@ def test_bicubic_constant_and_mirror():
     up = bicubic.upsample(y, 14, 20)
     upm = bicubic.upsample(y[:, ::-1, ::-1], 14, 20)
     assert np.abs(up[:, ::-1, ::-1] - upm).max() <= 1e-14
+
+
+def test_area_downscale_matches_torch_adaptive_pool():
+    from oracle import area
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0, 1, size=(3, 37, 53))
+    for (H, W) in [(18, 26), (37, 53), (9, 13), (19, 27), (5, 40)]:
+        ref = F.adaptive_avg_pool2d(torch.tensor(x)[None], (H, W))[0].numpy()
+        assert np.abs(area.downscale(x, H, W) - ref).max() <= 1e-13
+
+
+def test_area_downscale_integer_factor_is_box_mean():
+    from oracle import area
+    rng = np.random.default_rng(9)
+    x = rng.uniform(0, 1, size=(3, 16, 24))
+    y = area.downscale(x, 4, 6)
+    ref = x.reshape(3, 4, 4, 6, 4).mean(axis=(2, 4))
+    assert np.abs(y - ref).max() <= 1e-15
+    assert abs(y.mean() - x.mean()) <= 1e-14          # mean preserved for exact factors

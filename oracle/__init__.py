@@ -77,6 +77,9 @@ def lib():
                                                   dp, dp, dp, dp, ctypes.c_double, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
                                                   dp, dp]
+            L.orc_relu11.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_block_style_grad.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, dp,
+                                               dp, dp]
             L.orc_table1_mean.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
                                           dp, dp]
             L.orc_table1_std.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
@@ -299,3 +302,32 @@ def table1_std(V, sigma, w):
     lib().orc_table1_std(_p(V), npx, nc, _p(np.ascontiguousarray(sigma, np.float64)), float(w),
                          _p(E), _p(g))
     return float(E[0]), g
+
+
+def relu11_gram(P, x, strip=192):
+    """G^{ReLU1_1}(x) = V V^T / n_p of a large image, strip by strip: conv1_1 features of each
+    row strip (with a 1-row halo on each side, dropped afterwards) summed with numpy in FP64."""
+    x = _img(x)
+    _, H, W = x.shape
+    S = np.zeros((64, 64))
+    for y0 in range(0, H, strip):
+        y1 = min(H, y0 + strip)
+        a, b = max(0, y0 - 1), min(H, y1 + 1)
+        blk = np.ascontiguousarray(x[:, a:b])
+        out = np.zeros((64, b - a, W))
+        _check(lib().orc_relu11(_p(P), _p(blk), b - a, W, _p(out)))
+        V = out[:, y0 - a:y0 - a + (y1 - y0)].reshape(64, -1)
+        S += V @ V.T
+    return S / (H * W)
+
+
+def block_style_grad(P, blk, G_glob, G_ref, np_glob, w_style):
+    """Algorithm 1, Step 2 for one block with the given global statistics (no content term)."""
+    blk = _img(blk)
+    _, h, w = blk.shape
+    out = np.zeros((3, h, w))
+    _check(lib().orc_block_style_grad(_p(P), _p(blk), h, w, _p(join_grams(G_glob)),
+                                      _p(join_grams(G_ref)),
+                                      _p(np.ascontiguousarray(np_glob, np.float64)),
+                                      _p(np.ascontiguousarray(w_style, np.float64)), _p(out)))
+    return out

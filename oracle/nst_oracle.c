@@ -811,5 +811,45 @@ int orc_loss_grad_tiled(const double *params, const double *x, int H, int W,
                                  NULL, lambda_c, k_h, k_w, m1, m2, E_out, grad, parts, grams_out);
 }
 
+/* ReLU1_1 features of x alone (3 x H x W -> 64 x H x W), rounded as stored in storage mode */
+int orc_relu11(const double *params, const double *x, int H, int W, double *out) {
+  if (H < 1 || W < 1) return ORC_ERR_SHAPE;
+  const double *Wp[NCONV], *bp[NCONV];
+  param_ptrs(params, Wp, bp);
+  conv3x3_forward(x, 3, H, W, Wp[0], bp[0], 64, out, 0);
+  relu_inplace(out, 64L * H * W);
+  q_array(out, 64L * H * W);
+  return ORC_OK;
+}
+
+/* Step 2 of Algorithm 1 for ONE block, given the global statistics: blk is the block extracted
+ * with its margin (3 x h x w); G_glob holds G^L(x) of the whole image (np_glob[L] feature pixels)
+ * and G_ref the style Grams. Feature gradients are formed on the whole block (Table 1 row 2) and
+ * back-propagated; dblk receives dE/d(blk). The content term is left out (lambda_c = 0). The
+ * caller keeps the inner part. */
+int orc_block_style_grad(const double *params, const double *blk, int h, int w,
+                         const double *G_glob, const double *G_ref, const double *np_glob,
+                         const double *w_style, double *dblk) {
+  if (check_size(h, w) && (h < 1 || w < 1)) return ORC_ERR_SHAPE;
+  acts_t A;
+  if (acts_alloc(&A, h, w)) return ORC_ERR_OOM;
+  vgg_forward(params, blk, &A);
+  double *fg[NCONV] = {0};
+  long off = 0;
+  for (int s = 0; s < NSTYLE; s++) {
+    int l = kStyleConv[s], c = kCout[l];
+    long npix = (long)A.h[l] * A.w[l];
+    if (w_style[s] != 0.0 && npix > 0) {
+      fg[l] = (double *)malloc(sizeof(double) * (size_t)c * npix + 8);
+      gram_loss_grad(A.a[l], c, npix, np_glob[s], G_glob + off, G_ref + off, w_style[s], fg[l]);
+    }
+    off += (long)c * c;
+  }
+  int rc = vgg_backward(params, &A, fg, dblk);
+  for (int l = 0; l < NCONV; l++) free(fg[l]);
+  acts_free(&A);
+  return rc;
+}
+
 /* the oracle's block partition, exposed for tests */
 int orc_plan_1d(int L, int k, int *b) { return plan_1d(L, k, b); }

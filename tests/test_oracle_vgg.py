@@ -183,3 +183,24 @@ def test_algorithm1_gradient_exact_with_margin():
     assert rel_l2(g2, g0) > 1e-9
     _, g3, _, _ = oracle.loss_grad_tiled(P, x, ct, Gv, W_STYLE, LAMBDA_C, (1, 2), (0, 0))
     assert rel_l2(g3, g0) > 1e-2
+
+
+def test_strip_gram_and_single_block_step2_agree_with_untiled():
+    """The helpers used by the full-size sampled GPU checks: the strip-wise ReLU1_1 Gram equals
+    the untiled one, and Step 2 on a 5 x 5 block (margin 2 = the ReLU1_1 term's reach) gives
+    the untiled gradient of the ReLU1_1 term at the block centre."""
+    params, P, u, v = problem(64, 96, seed=11)
+    ws = np.array([0.2, 0, 0, 0, 0])
+    ct = oracle.content_target(P, u)
+    Gv = oracle.style_grams(P, v)
+    E, g, _, Gx = oracle.loss_grad(P, u, ct, Gv, ws, 0.0)
+    G1 = oracle.relu11_gram(P, u, strip=10)
+    assert np.allclose(G1, Gx[0], rtol=1e-12, atol=1e-15)
+    zeros = [np.zeros((c, c)) for c in oracle.STYLE_CHANNELS]
+    Gglob = [G1] + zeros[1:]
+    npg = [64 * 96, 1, 1, 1, 1]
+    for (py, px) in [(30, 40), (2, 5), (63, 95), (10, 0)]:
+        y0, y1, x0, x1 = max(0, py - 2), min(64, py + 3), max(0, px - 2), min(96, px + 3)
+        d = oracle.block_style_grad(P, u[:, y0:y1, x0:x1], Gglob, Gv, npg, ws)
+        assert np.allclose(d[:, py - y0, px - x0], g[:, py, px], rtol=1e-10,
+                           atol=1e-12 * np.abs(g).max())

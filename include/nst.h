@@ -148,6 +148,12 @@ nst_status nst_tile_plan(int H, int W, int tiles_h, int tiles_w, int margin, int
  * iteration. FP32 vectors, FP64 dot products, all on the device (no host round trip).
  * State (history 2 m n floats) is owned by the nst_lbfgs object, allocated at create. */
 nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m);
+/* As nst_lbfgs_create, with flags. NST_LBFGS_HOST_HISTORY keeps the 2 (m + 1) history vectors in
+ * page-locked host memory mapped into the device address space (on a Grace-Blackwell node the
+ * two-loop kernels read them over NVLink-C2C): the GPU analogue of the paper's moving the L-BFGS
+ * history to the CPU at the last scale to free device memory (Section 5.1). Same results. */
+enum { NST_LBFGS_HOST_HISTORY = 1 };
+nst_status nst_lbfgs_create_ex(nst_lbfgs **out, long long n, int m, int flags);
 nst_status nst_lbfgs_destroy(nst_lbfgs *st);
 /* One iteration: given x (device, n floats, updated in place) and g = grad E(x) (device), form
  * the new pair from the previous call, compute d = -H g and set x <- x + t d. */

@@ -14,7 +14,8 @@ struct nst_lbfgs {
   long long stride = 0;              // slot stride: n rounded up to 64 floats (256-byte slots)
   int m = 0;
   long long iters = 0;
-  float *S = nullptr, *Y = nullptr;  // [m+1][n] history slots
+  float *S = nullptr, *Y = nullptr;  // [m+1][n] history slots (device pointers)
+  float *S_host = nullptr, *Y_host = nullptr;  // host allocations when the history lives there
   float *g_prev = nullptr, *q = nullptr;
   double *rho = nullptr, *alpha = nullptr, *partials = nullptr;
   LbfgsCtl *ctl = nullptr;
@@ -27,15 +28,36 @@ constexpr double kCurvEps = 1e-10;
 extern "C" {
 
 nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m) {
-  if (!out || n <= 0 || m < 1 || m > kMaxHistory) return NST_ERR_INVALID_ARG;
+  return nst_lbfgs_create_ex(out, n, m, 0);
+}
+
+nst_status nst_lbfgs_create_ex(nst_lbfgs **out, long long n, int m, int flags) {
+  if (!out || n <= 0 || m < 1 || m > kMaxHistory || (flags & ~NST_LBFGS_HOST_HISTORY))
+    return NST_ERR_INVALID_ARG;
   *out = nullptr;
   nst_lbfgs *st = new nst_lbfgs();
   st->n = n;
   st->m = m;
   st->stride = (n + 63) / 64 * 64;
   const size_t slots = (size_t)(m + 1);
-  bool ok = cudaMalloc(&st->S, slots * st->stride * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&st->Y, slots * st->stride * sizeof(float)) == cudaSuccess &&
+  const size_t hist = slots * st->stride * sizeof(float);
+  bool ok = true;
+  if (flags & NST_LBFGS_HOST_HISTORY) {
+    ok = cudaHostAlloc(&st->S_host, hist, cudaHostAllocMapped | cudaHostAllocPortable) ==
+             cudaSuccess &&
+         cudaHostAlloc(&st->Y_host, hist, cudaHostAllocMapped | cudaHostAllocPortable) ==
+             cudaSuccess &&
+         cudaHostGetDevicePointer(&st->S, st->S_host, 0) == cudaSuccess &&
+         cudaHostGetDevicePointer(&st->Y, st->Y_host, 0) == cudaSuccess;
+    if (ok) {
+      std::memset(st->S_host, 0, hist);
+      std::memset(st->Y_host, 0, hist);
+    }
+  } else {
+    ok = cudaMalloc(&st->S, hist) == cudaSuccess && cudaMalloc(&st->Y, hist) == cudaSuccess;
+    if (ok) ok = cudaMemset(st->S, 0, hist) == cudaSuccess && cudaMemset(st->Y, 0, hist) == cudaSuccess;
+  }
+  ok = ok &&
             cudaMalloc(&st->g_prev, n * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&st->q, n * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&st->rho, slots * sizeof(double)) == cudaSuccess &&
@@ -46,8 +68,6 @@ nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m) {
     nst_lbfgs_destroy(st);
     return NST_ERR_OOM;
   }
-  cudaMemset(st->S, 0, slots * st->stride * sizeof(float));
-  cudaMemset(st->Y, 0, slots * st->stride * sizeof(float));
   cudaMemset(st->rho, 0, slots * sizeof(double));
   cudaMemset(st->alpha, 0, (size_t)m * sizeof(double));
   LbfgsCtl c;
@@ -70,7 +90,14 @@ nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m) {
 nst_status nst_lbfgs_destroy(nst_lbfgs *st) {
   if (!st) return NST_OK;
   cudaDeviceSynchronize();
-  cudaFree(st->S); cudaFree(st->Y); cudaFree(st->g_prev); cudaFree(st->q);
+  if (st->S_host) {
+    cudaFreeHost(st->S_host);
+    cudaFreeHost(st->Y_host);
+  } else {
+    cudaFree(st->S);
+    cudaFree(st->Y);
+  }
+  cudaFree(st->g_prev); cudaFree(st->q);
   cudaFree(st->rho); cudaFree(st->alpha); cudaFree(st->partials); cudaFree(st->ctl);
   delete st;
   return NST_OK;

@@ -45,9 +45,10 @@ def nst_loss(x, nst_ctx):
     return NSTLossFunction.apply(x, nst_ctx)
 
 
-def style_transfer(nst_ctx, x, iters, history=10, callback=None):
-    """L-BFGS on E (Section 3.1) from x (updated in place), `iters` evaluations."""
-    opt = native.LBFGS(x.numel(), history)
+def style_transfer(nst_ctx, x, iters, history=10, callback=None, host_history=False):
+    """L-BFGS on E (Section 3.1) from x (updated in place), `iters` evaluations. host_history
+    keeps the L-BFGS history in mapped host memory (Section 5.1, last scale)."""
+    opt = native.LBFGS(x.numel(), history, host_history=host_history)
     grad = torch.empty_like(x)
     loss = torch.zeros(1, dtype=torch.float64, device=x.device)
     for k in range(iters):
@@ -79,7 +80,7 @@ def scaled(n, f):
 
 
 def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callback=None,
-               **cfg):
+               host_history_last=False, **cfg):
     """Algorithm 2: for s = 1..n, downscale (u, v) by 2^(n-s) (area averaging, sizes rounded);
     x = u at the first scale, else the previous x upscaled by 2 (bicubic); then L-BFGS with
     localized gradients (history 100 at the first scale, 10 afterwards).
@@ -98,7 +99,8 @@ def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callb
         ctx.style_targets(vs)
         ctx.content_targets(us)
         style_transfer(ctx, x, schedule[s - 1], history=100 if s == 1 else 10,
-                       callback=(lambda k, l, s=s: callback(s, k, l)) if callback else None)
+                       callback=(lambda k, l, s=s: callback(s, k, l)) if callback else None,
+                       host_history=host_history_last and s == n_scales)
         ctx.close()
     return x
 

@@ -72,6 +72,7 @@ def lib():
                 "nst_last_error": ([vp], ctypes.c_char_p),
                 "nst_tile_plan": ([ip, ip, ip, ip, ip, vp], ip),
                 "nst_lbfgs_create": ([ctypes.POINTER(vp), ll, ip], ip),
+                "nst_lbfgs_create_ex": ([ctypes.POINTER(vp), ll, ip, ip], ip),
                 "nst_lbfgs_destroy": ([vp], ip),
                 "nst_lbfgs_step": ([vp, fp, fp, vp], ip),
                 "nst_lbfgs_info": ([vp, ctypes.POINTER(ctypes.c_int),
@@ -231,9 +232,12 @@ def split_grams(flat):
 class LBFGS:
     """Device-resident L-BFGS state (nst_lbfgs)."""
 
-    def __init__(self, n, m):
+    HOST_HISTORY = 1
+
+    def __init__(self, n, m, host_history=False):
         h = ctypes.c_void_p()
-        _check(lib().nst_lbfgs_create(ctypes.byref(h), int(n), int(m)))
+        _check(lib().nst_lbfgs_create_ex(ctypes.byref(h), int(n), int(m),
+                                         self.HOST_HISTORY if host_history else 0))
         self.h = h
         self.n = n
 

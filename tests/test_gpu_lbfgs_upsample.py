@@ -83,3 +83,21 @@ def test_downscale_matches_oracle(h, w, H, W):
         assert np.abs(got[:, rows] - full[:, rows]).max() <= 2e-6
     else:
         assert np.abs(got - area.downscale(x.astype(np.float64), H, W)).max() <= 2e-6
+
+
+def test_lbfgs_host_history_gives_identical_iterates():
+    """History in mapped host memory (the paper's CPU-side history of the last scale, Section
+    5.1): the same kernels on the same values, so the iterates are bit-identical."""
+    n, m = 20001, 7
+    rng = np.random.default_rng(5)
+    d = torch.tensor(rng.uniform(0.5, 2.0, size=n), dtype=torch.float32, device="cuda")
+    b = torch.tensor(rng.standard_normal(n), dtype=torch.float32, device="cuda")
+    xs = []
+    for host in (False, True):
+        x = torch.zeros(n, device="cuda")
+        st = native.LBFGS(n, m, host_history=host)
+        for _ in range(15):
+            st.step(x, d * x - b)
+        xs.append(x.clone())
+        st.close()
+    assert torch.equal(xs[0], xs[1])

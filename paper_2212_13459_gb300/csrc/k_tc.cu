@@ -133,26 +133,33 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
 // writes the pooled value (the BF16 values, exactly as stored, so the result equals pooling the
 // stored activation). Outside the block's valid pooled region the pooled map is zero.
 __device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGeom &g, int b,
-                                                int y, int x, int n, int tw, float *v) {
+                                                int y, int x, int n, int tw, const float *v) {
+  // the stored BF16 values, two channels per register; max over the window with 2 shuffles
+  uint32_t h[16];
 #pragma unroll
-  for (int j = 0; j < 32; j++) {
-    float f = __bfloat162float(__float2bfloat16_rn(v[j]));
-    f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, 1));
-    f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, tw));
-    v[j] = f;
+  for (int j = 0; j < 16; j++) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    h[j] = *reinterpret_cast<uint32_t *>(&p);
+  }
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    uint32_t o1 = __shfl_xor_sync(0xffffffffu, h[j], 1);
+    __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162 *>(&h[j]),
+                               *reinterpret_cast<__nv_bfloat162 *>(&o1));
+    uint32_t mu = *reinterpret_cast<uint32_t *>(&m);
+    uint32_t o2 = __shfl_xor_sync(0xffffffffu, mu, tw);
+    m = __hmax2(m, *reinterpret_cast<__nv_bfloat162 *>(&o2));
+    h[j] = *reinterpret_cast<uint32_t *>(&m);
   }
   if ((y & 1) || (x & 1) || y >= a.Hb || x >= a.Wb) return;
   const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
   const bool valid = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
-  __nv_bfloat16 *out =
-      reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + (((size_t)b * Hp + py) * Wp + px) * a.cout + n;
+  uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) +
+                                         (((size_t)b * Hp + py) * Wp + px) * a.cout + n);
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
-    float w8[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++) w8[j] = valid ? v[8 * q + j] : 0.f;
-    st_bf16x8(out + 8 * q, w8);
-  }
+  for (int q = 0; q < 4; q++)
+    out[q] = valid ? make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3])
+                   : make_uint4(0u, 0u, 0u, 0u);
 }
 
 // ---- the kernel -------------------------------------------------------------------------------------
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
       tc_fence_after();
       const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
       const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
@@ -336,13 +343,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const TcGeom tg) {
   using Cfg = HaloCfg<BN, KB, P2KB, NT>;
   constexpr int STAGES = Cfg::STAGES;
-  constexpr uint32_t TMEM_COLS = 2 * BN;
+  // accumulators in TMEM: four for the 64-wide slices (their tiles are short, so more tiles in
+  // flight keep the tensor pipe fed while the epilogue drains), two otherwise
+  constexpr int NACC = BN == 64 ? 4 : 2;
+  constexpr uint32_t TMEM_COLS = NACC * BN;
   constexpr uint32_t IDESC = make_idesc(BN);
   constexpr int KBT = KB + P2KB;   // K-blocks per tile
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], w_bar;
-  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ __align__(8) uint64_t tfull_bar[NACC], tempty_bar[NACC];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     mbar_init(smem_u32(&w_bar), 1);
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < NACC; i++) {
       mbar_init(smem_u32(&tfull_bar[i]), 1);
       mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads);
     }
@@ -413,8 +423,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int it = 0;
       for (int t = m_first; t < m_total && ok; t += m_step, it++) {
-        const int acc = it & 1;
-        const uint32_t use = (uint32_t)(it >> 1);
+        const int acc = it % NACC;
+        const uint32_t use = (uint32_t)(it / NACC);
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * BN);
@@ -454,9 +464,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     int it = 0;
     for (int t = m_first; t < m_total; t += m_step, it++) {
-      const int acc = it & 1;
-      const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      const int acc = it % NACC;
+      const uint32_t use = (uint32_t)(it / NACC);
+      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
       tc_fence_after();
       const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
       const int b = t / (tg.tiles_x * tg.tiles_y);

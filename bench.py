@@ -2,7 +2,7 @@
 """Throughput of the localized style-transfer loss + image-gradient evaluation (Algorithm 1).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload scale3|scale4|scale1] [--precision bf16|fp32]
+                    [--workload scale3|scale4|scale2|scale1] [--precision bf16|fp32]
 
 A step is one evaluation of E(x) and dE/dx through the C ABI (nst_loss_grad): both passes over
 all blocks with margins, every kernel of the path. The default workload is the 3024 x 4032 scale
@@ -41,6 +41,7 @@ FLOP_PER_PX = 2 * 722304 + 722304 + 2 * 34816
 WORKLOADS = {
     "scale3": dict(H=3024, W=4032, Hv=2113, Wv=2660, seed=3, tiles=8, small=(1512, 2016)),
     "scale4": dict(H=6048, W=8064, Hv=4226, Wv=5319, seed=4, tiles=16, small=(3024, 4032)),
+    "scale2": dict(H=1512, W=2016, Hv=1057, Wv=1330, seed=5, tiles=4, small=(756, 1008)),
     "scale1": dict(H=756, W=1008, Hv=1057, Wv=1330, seed=2, tiles=1, small=None),
 }
 
@@ -307,7 +308,8 @@ def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E
     if prec == native.PREC_BF16 and conv_tflops:
         roofline = {"bound": "tensor", "kernel": "conv_tc_kernel (tcgen05 implicit-GEMM conv)",
                     "achieved": conv_tflops, "peak": peak_conv, "unit": "TFLOP/s",
-                    "frac": conv_tflops / peak_conv, "traffic": read_traffic(),
+                    "frac": conv_tflops / peak_conv,
+                    "traffic": read_traffic(tm["conv_flops"] / max(1, tm["conv_launches"])),
                     "peak_source": "%s bf16_tflops_sustained" % peaks["source"],
                     "launches_per_step": tm["conv_launches"] / args.steps,
                     "ms_per_step": tm["conv_ms"] / args.steps,
@@ -378,9 +380,11 @@ def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev):
             "bf16_speedup": None, "bf16_grad_rel_err_vs_fp32": rel, "loss_fp32": loss.item()}
 
 
-def read_traffic():
-    """DRAM bytes per launch of the convolution kernel from the committed ncu summary, if its
-    recorded source hash matches the current kernel source; else None."""
+def read_traffic(flops_per_launch):
+    """DRAM bytes per convolution launch: the committed ncu summary's DRAM bytes per executed
+    FLOP over every tcgen05 convolution launch of a smaller workload with the same block size,
+    times this run's FLOPs per launch; None when the summary was taken on another version of the
+    kernel source."""
     import hashlib
     src = os.path.join(ROOT, "paper_2212_13459_gb300", "csrc", "k_tc.cu")
     summ = os.path.join(ROOT, "profiles", "conv_tc_traffic.txt")
@@ -388,7 +392,7 @@ def read_traffic():
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         kv = dict(line.strip().split("=", 1) for line in open(summ) if "=" in line)
         if kv.get("k_tc_sha256_16") == h:
-            return float(kv["dram_bytes_per_launch"])
+            return float(kv["dram_bytes_per_flop"]) * flops_per_launch
     except Exception:
         pass
     return None

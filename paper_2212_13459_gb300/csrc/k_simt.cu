@@ -580,13 +580,13 @@ void launch_gram_reduce(const float *part, int nchunks, int C, double *Gacc, cud
 
 // ---- style finalisation: G = Gacc / np, E_L = w ||G - Ghat||^2, R = (4 w / np)(G - Ghat) -------------
 // One CTA of 1024 threads per style layer; deterministic reduction.
-__global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs a) {
-  __shared__ double red[1024];
-  __shared__ double beta_s[512];
+// Stage 1 (one CTA per layer): mean / std terms of Eq. 5 per channel, from the channel sums and
+// diag(G): beta_j (added to R's diagonal), alpha_j (epilogue offset), the moment loss, and the
+// moments themselves when requested.
+__global__ void __launch_bounds__(512) style_moments_kernel(StyleFinalizeArgs a) {
+  __shared__ double red[512];
   const StyleLayerArgs L = a.L[blockIdx.x];
-  const long long n = (long long)L.C * L.C;
-  const double inv = 1.0 / L.np, rs = 4.0 * L.w / L.np;
-  // mean / std terms (Eq. 5): per channel, from the channel sums and diag(G)
+  const double inv = 1.0 / L.np;
   double s = 0.0;
   for (int j = threadIdx.x; j < L.C; j += blockDim.x) {
     double b = 0.0;
@@ -604,16 +604,34 @@ __global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs 
         if (L.alpha) L.alpha[j] = (float)(L.wm * 2.0 * inv * (m - L.mu[j]) - b * m);
       }
     }
-    beta_s[j] = b;
+    a.beta[blockIdx.x * 512 + j] = b;
   }
+  red[threadIdx.x] = s;
   __syncthreads();
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+  for (int k = 256; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.partial[blockIdx.x * kFinalizeChunks] = red[0];
+}
+
+// Stage 2 (grid: layer x chunk): G = Gacc / np, R = (4 w / np)(G - Ghat) + diag(beta), and the
+// chunk's share of w ||G - Ghat||^2 into partial[layer][1 + chunk]
+__global__ void __launch_bounds__(256) style_residual_kernel(StyleFinalizeArgs a) {
+  __shared__ double red[256];
+  const StyleLayerArgs L = a.L[blockIdx.x];
+  const long long n = (long long)L.C * L.C;
+  const long long per = (n + gridDim.y - 1) / gridDim.y;
+  const long long e0 = blockIdx.y * per, e1 = e0 + per < n ? e0 + per : n;
+  const double inv = 1.0 / L.np, rs = 4.0 * L.w / L.np;
+  double s = 0.0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const double G = L.Gacc[e] * inv;
     const double d = G - L.Ghat[e];
     L.Gout[e] = G;
     s += L.w * d * d;
     const int i = (int)(e / L.C), j = (int)(e % L.C);
-    const double r = rs * d + (i == j ? beta_s[j] : 0.0);
+    const double r = rs * d + (i == j ? a.beta[blockIdx.x * 512 + j] : 0.0);
     if (a.r_is_bf16)
       reinterpret_cast<__nv_bfloat16 *>(L.R)[e] = __float2bfloat16_rn((float)r);
     else
@@ -621,11 +639,27 @@ __global__ void __launch_bounds__(1024) style_finalize_kernel(StyleFinalizeArgs 
   }
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int k = 512; k > 0; k >>= 1) {
+  for (int k = 128; k > 0; k >>= 1) {
     if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.Eparts[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) a.partial[blockIdx.x * kFinalizeChunks + 1 + blockIdx.y] = red[0];
+}
+
+// Stage 3: E_L = sum of the layer's partials in a fixed order
+__global__ void style_sum_kernel(StyleFinalizeArgs a, int chunks) {
+  const int l = threadIdx.x;
+  if (l < kNStyle) {
+    double s = 0.0;
+    for (int c = 0; c <= chunks; c++) s += a.partial[l * kFinalizeChunks + c];
+    a.Eparts[l] = s;
+  }
+}
+
+void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s) {
+  style_moments_kernel<<<kNStyle, 512, 0, s>>>(a);
+  style_residual_kernel<<<dim3(kNStyle, kFinalizeChunks - 1), 256, 0, s>>>(a);
+  style_sum_kernel<<<1, 32, 0, s>>>(a, kFinalizeChunks - 1);
 }
 
 // channel sums over owned pixels: partial[c][j] = sum over chunk c of V[p][j] (FP32 runs of 64
@@ -675,9 +709,6 @@ template void launch_chansum<__nv_bfloat16>(const __nv_bfloat16 *, int, int, int
                                             const OwnRect *, const GramChunk *, int, double *,
                                             double *, cudaStream_t);
 
-void launch_style_finalize(const StyleFinalizeArgs &a, cudaStream_t s) {
-  style_finalize_kernel<<<kNStyle, 1024, 0, s>>>(a);
-}
 
 // ---- content loss over owned pixels: partial[c] = sum (V - Vu)^2 (FP64) ----------------------------
 template <typename T>
@@ -699,11 +730,15 @@ __global__ void __launch_bounds__(256) content_partial_kernel(
     float a[8], t[8];
     load8(V + (((size_t)ch.b * Hb + y) * Wb + x) * 512 + c, a);
     load8(Vu + ((size_t)(oy + y) * Wc + ox + x) * 512 + c, t);
+    // differences of two stored values are exact in FP32 (BF16 inputs) or nearly so (FP32
+    // inputs); 8 squares summed in FP32, then accumulated in FP64
+    float f = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-      const double d = (double)a[j] - (double)t[j];
-      s += d * d;
+      const float d = a[j] - t[j];
+      f = fmaf(d, d, f);
     }
+    s += (double)f;
   }
   red[threadIdx.x] = s;
   __syncthreads();

@@ -436,16 +436,26 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t sa = a_base + stage * kHaloStage;
-          const int tap0 = kb < KB ? 0 : 4, tap1 = kb < KB ? 9 : 5;   // phase 2: centre only
-          for (int tap = tap0; tap < tap1; tap++) {
-            const int dy = tap / 3, dx = tap % 3;   // box offsets 0..2 (= tap offset + 1)
-            // shifted by whole 128-byte rows; the swizzle follows absolute address bits, so the
-            // phase field stays 0 (the box itself starts 1024-aligned)
-            const uint32_t start = sa + (uint32_t)((dy * kHaloBoxW + dx) * 128);
-            const uint64_t da = sw128_desc_k(start, kHaloBoxW * 128, 0);
-            const uint32_t wt = kb < KB ? w_base + (tap * KB + kb) * Cfg::TILE_B
-                                        : w_base + (9 * KB + kb - KB) * Cfg::TILE_B;
-            const uint64_t db = sw128_desc(wt);
+          // shifted by whole 128-byte rows; the swizzle follows absolute address bits, so the
+          // phase field stays 0 (the box itself starts 1024-aligned). Descriptors are the stage's
+          // base descriptors plus compile-time offsets (address field in 16-byte units).
+          const uint64_t da0 = sw128_desc_k(sa, kHaloBoxW * 128, 0);
+          if (kb < KB) {
+            const uint64_t db0 = sw128_desc(w_base + kb * Cfg::TILE_B);
+#pragma unroll
+            for (int tap = 0; tap < 9; tap++) {
+              const uint64_t da = da0 + (uint64_t)(((tap / 3) * kHaloBoxW + tap % 3) * 8);
+              const uint64_t db = db0 + (uint64_t)(tap * KB * (Cfg::TILE_B >> 4));
+#pragma unroll
+              for (int k = 0; k < kBK / 16; k++) {
+                mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
+                         first ? 0u : 1u);
+                first = false;
+              }
+            }
+          } else {   // phase 2: the V R term, centre tap only
+            const uint64_t da = da0 + (uint64_t)((kHaloBoxW + 1) * 8);
+            const uint64_t db = sw128_desc(w_base + (9 * KB + kb - KB) * Cfg::TILE_B);
 #pragma unroll
             for (int k = 0; k < kBK / 16; k++) {
               mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, first ? 0u : 1u);

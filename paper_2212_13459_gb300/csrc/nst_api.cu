@@ -174,6 +174,7 @@ struct nst_ctx {
   double *d_sacc = nullptr, *d_mu = nullptr, *d_sigma = nullptr, *d_cspart = nullptr;
   float *d_alpha = nullptr;
   size_t cspart_cap = 0;
+  double *d_fin = nullptr;   // style finaliser scratch: beta [5][512] then partials
   // workspace (grow-only)
   void *d_ws = nullptr;
   size_t ws_cap = 0;
@@ -691,6 +692,8 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   }
   fa.Eparts = ctx->d_parts;
   fa.r_is_bf16 = ctx->bf16 ? 1 : 0;
+  fa.beta = ctx->d_fin;
+  fa.partial = ctx->d_fin + kNStyle * 512;
   ctx->launches++;
   launch_style_finalize(fa, s);
   // Step 2: loss and gradient block by block
@@ -864,7 +867,9 @@ nst_status nst_create(nst_ctx **out, const float *params, long long n_params,
       cudaMalloc(&ctx->d_sacc, sizeof(double) * kMomentTotal) != cudaSuccess ||
       cudaMalloc(&ctx->d_mu, sizeof(double) * kMomentTotal) != cudaSuccess ||
       cudaMalloc(&ctx->d_sigma, sizeof(double) * kMomentTotal) != cudaSuccess ||
-      cudaMalloc(&ctx->d_alpha, sizeof(float) * kMomentTotal) != cudaSuccess)
+      cudaMalloc(&ctx->d_alpha, sizeof(float) * kMomentTotal) != cudaSuccess ||
+      cudaMalloc(&ctx->d_fin, sizeof(double) * (kNStyle * 512 + kNStyle * kFinalizeChunks)) !=
+          cudaSuccess)
     return bad(NST_ERR_OOM);
   for (int i = 0; i < 5; i++) ctx->aug |= cfg->w_mean[i] != 0.f || cfg->w_std[i] != 0.f;
   cudaMemset(ctx->d_err, 0, sizeof(unsigned));
@@ -891,6 +896,7 @@ nst_status nst_destroy(nst_ctx *ctx) {
   cudaFree(ctx->d_xh); cudaFree(ctx->d_gh);
   cudaFree(ctx->d_sacc); cudaFree(ctx->d_mu); cudaFree(ctx->d_sigma); cudaFree(ctx->d_alpha);
   cudaFree(ctx->d_cspart);
+  cudaFree(ctx->d_fin);
   for (auto &kv : ctx->plans) {
     cudaFree(kv.second.d_geom);
     cudaFree(kv.second.d_own);
@@ -931,6 +937,8 @@ nst_status nst_style_targets(nst_ctx *ctx, const float *v, int Hv, int Wv, void 
   }
   fa.Eparts = ctx->d_parts;
   fa.r_is_bf16 = ctx->bf16 ? 1 : 0;
+  fa.beta = ctx->d_fin;
+  fa.partial = ctx->d_fin + kNStyle * 512;
   launch_style_finalize(fa, s);
   CK(cudaGetLastError());
   ctx->have_style = true;

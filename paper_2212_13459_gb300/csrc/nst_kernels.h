@@ -27,10 +27,13 @@ struct StyleLayerArgs {
   float *alpha;
   double *mean_out, *std_out;
 };
+constexpr int kFinalizeChunks = 65;   // per layer: moment term + 64 residual chunks
 struct StyleFinalizeArgs {
   StyleLayerArgs L[kNStyle];
-  double *Eparts;  // [5]
+  double *Eparts;   // [5]
   int r_is_bf16;
+  double *beta;     // scratch [5][512]
+  double *partial;  // scratch [5][kFinalizeChunks]
 };
 
 // conv1_1 weights and biases as one kernel parameter (7,168 bytes): w[k][c] = W1[c][k] with

@@ -34,8 +34,9 @@
  * Storage precision (orc_set_storage): the network's gradient is discontinuous where a ReLU input
  * or a pooling window's top two values meet, so a ReLU mask or pooling argmax decided in one
  * precision cannot be compared with one decided in another. In mode 1 (float32) or 2 (bfloat16)
- * the oracle rounds, round-to-nearest-even, every value the evaluated form stores: the weights of
- * conv1_2..conv5_1 (bfloat16 mode only), every post-ReLU activation, the style residuals
+ * the oracle rounds, round-to-nearest-even, every value the evaluated form stores: the image as
+ * it enters conv1_1 (bfloat16 mode only: a hi + lo pair of bfloat16 numbers), the weights of
+ * all thirteen convolutions (bfloat16 mode only), every post-ReLU activation, the style residuals
  * R_L = 4 w_L (G - G_ref) / n_p, and every masked feature gradient before it enters the next
  * transposed convolution; the reverse pass stays the exact adjoint of the rounded forward values.
  * Mode 0 (the default) is the plain FP64 definition.
@@ -84,8 +85,18 @@ static void q_array(double *a, long n) {
   if (g_storage)
     for (long i = 0; i < n; i++) a[i] = q(a[i]);
 }
-/* weights of conv1_2..conv5_1 are stored in bfloat16 by the bfloat16 form */
-static double qw(double w, int layer) { return (g_storage == 2 && layer > 0) ? q(w) : w; }
+/* the bfloat16 form stores the weights of every convolution in bfloat16 */
+static double qw(double w, int layer) {
+  (void)layer;
+  return g_storage == 2 ? q(w) : w;
+}
+
+/* the bfloat16 form reads the image as a pair of bfloat16 numbers: hi = bf16(v), lo = bf16(v - hi);
+ * the pair carries v to within 2^-17 |v| */
+static double q_pair(double v) {
+  const double hi = q(v);
+  return hi + q(v - hi);
+}
 
 static int imin(int a, int b) { return a < b ? a : b; }
 static int imax(int a, int b) { return a > b ? a : b; }
@@ -117,6 +128,14 @@ static void param_ptrs(const double *params, const double **W, const double **b)
 static void conv3x3_forward(const double *in, int cin, int h, int w, const double *W,
                             const double *b, int cout, double *out, int layer) {
   long hw = (long)h * w;
+  double *in_pair = NULL;
+  if (layer == 0 && g_storage == 2) {
+    in_pair = (double *)malloc(sizeof(double) * (size_t)cin * hw + 8);
+    if (in_pair) {
+      for (long i = 0; i < cin * hw; i++) in_pair[i] = q_pair(in[i]);
+      in = in_pair;
+    }
+  }
 #pragma omp parallel for schedule(static)
   for (int co = 0; co < cout; co++) {
     double *o = out + co * hw;
@@ -137,6 +156,7 @@ static void conv3x3_forward(const double *in, int cin, int h, int w, const doubl
         }
     }
   }
+  free(in_pair);
 }
 
 /* Adjoint of conv3x3_forward with respect to its input:

@@ -191,7 +191,9 @@ template void launch_conv_simt<__nv_bfloat16>(const ConvArgs &, cudaStream_t);
 // block's extended rectangle of x and reads zero outside it (the block is a standalone image).
 // One thread computes all 64 channels of one pixel. The 27 x 64 weights travel as a
 // __grid_constant__ kernel parameter: with the loops unrolled, every FMA takes its weight
-// straight from the constant bank, so no load instruction competes with the FMAs.
+// straight from the constant bank, so no load instruction competes with the FMAs. In the BF16 form
+// each image value enters as hi + lo (hi = bf16(x), lo = bf16(x - hi)), the representation the
+// tensor-core conv1_1 multiplies, so both engines see the same input.
 template <typename T>
 __global__ void __launch_bounds__(128) conv11_fwd_kernel(const float *__restrict__ img, int H,
                                                          int W, const __grid_constant__ Conv11W cw,
@@ -215,8 +217,12 @@ __global__ void __launch_bounds__(128) conv11_fwd_kernel(const float *__restrict
           for (int kx = 0; kx < 3; kx++) {
             const int yy = y + ky - 1, xx = x + kx - 1;
             const bool ok = yy >= 0 && yy < g.eh && xx >= 0 && xx < g.ew;
-            in[ci * 9 + ky * 3 + kx] =
-                ok ? __ldg(img + ((size_t)ci * H + g.ey0 + yy) * W + g.ex0 + xx) : 0.f;
+            float v = ok ? __ldg(img + ((size_t)ci * H + g.ey0 + yy) * W + g.ex0 + xx) : 0.f;
+            if (sizeof(T) == 2) {   // the BF16 form reads the image as a BF16 pair hi + lo
+              const float hi = __bfloat162float(__float2bfloat16_rn(v));
+              v = hi + __bfloat162float(__float2bfloat16_rn(v - hi));
+            }
+            in[ci * 9 + ky * 3 + kx] = v;
           }
 #pragma unroll
       for (int c = 0; c < 64; c++) acc[c] = cw.b[c];

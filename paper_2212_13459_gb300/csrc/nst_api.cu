@@ -112,6 +112,7 @@ struct Batch {
   int chunk_off[kNStyle + 1], nchunks[kNStyle + 1];  // Gram chunks per style layer; [5] content
   int tc_off[kNStyle], tc_runs[kNStyle];      // tensor-core Gram runs per style layer
   int max_inner_px, max_content_px;
+  int max_inner_h, max_inner_w;
 };
 
 struct PassPlan {
@@ -245,6 +246,13 @@ uint16_t f2bf(float f) {
   return (uint16_t)(u >> 16);
 }
 
+float bf2f(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 // ---- pass plan --------------------------------------------------------------------------------------
 size_t tile_bytes(int Hb, int Wb, size_t esz) {
   size_t px = (size_t)Hb * Wb, tot = 0;
@@ -358,9 +366,12 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
     }
     bt.max_inner_px = 0;
     bt.max_content_px = 0;
+    bt.max_inner_h = bt.max_inner_w = 0;
     for (int i = t0; i < t0 + bt.B; i++) {
       const OwnRect &r = own[(size_t)kOwnInner * nt + i];
       bt.max_inner_px = std::max(bt.max_inner_px, (r.y1 - r.y0) * (r.x1 - r.x0));
+      bt.max_inner_h = std::max(bt.max_inner_h, r.y1 - r.y0);
+      bt.max_inner_w = std::max(bt.max_inner_w, r.x1 - r.x0);
       const OwnRect &c = own[(size_t)kOwnContent * nt + i];
       bt.max_content_px = std::max(bt.max_content_px, (c.y1 - c.y0) * (c.x1 - c.x0));
     }
@@ -457,7 +468,13 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
   {
     Timer tm(ctx, kTOther, s);
     ctx->launches++;
-    launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);
+    if (ctx->use_tc) {
+      cudaError_t e = launch_conv11_fwd_tc(img, p.H, p.W, ctx->d_w11, ctx->d_bias[0], geom, bt.B,
+                                           p.Hb, p.Wb, (__nv_bfloat16 *)ws.act[0], ctx->d_err, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "conv1_1 tensor-core forward launch");
+    } else {
+      launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);
+    }
   }
   for (int l = 1; l <= last_conv; l++) {
     const int lv = kLevel[l];
@@ -622,9 +639,16 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
   {
     Timer tm(ctx, kTOther, s);
     ctx->launches++;
-    launch_conv11_dgrad_scatter<T>((const T *)ws.g[cur], ctx->d_w11, geom,
-                                   p.d_own + (size_t)kOwnInner * nt + bt.t0, bt.B, p.Hb, p.Wb,
-                                   grad, p.H, p.W, bt.max_inner_px, s);
+    const OwnRect *inner = p.d_own + (size_t)kOwnInner * nt + bt.t0;
+    if (ctx->use_tc) {
+      cudaError_t e = launch_conv11_dgrad_tc((const __nv_bfloat16 *)ws.g[cur], ctx->d_w11, geom,
+                                             inner, bt.B, p.Hb, p.Wb, bt.max_inner_h,
+                                             bt.max_inner_w, grad, p.H, p.W, ctx->d_err, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "conv1_1 tensor-core input-gradient launch");
+    } else {
+      launch_conv11_dgrad_scatter<T>((const T *)ws.g[cur], ctx->d_w11, geom, inner, bt.B, p.Hb,
+                                     p.Wb, grad, p.H, p.W, bt.max_inner_px, s);
+    }
   }
   return NST_OK;
 }
@@ -825,13 +849,18 @@ nst_status nst_create(nst_ctx **out, const float *params, long long n_params,
     if (cudaMalloc(&ctx->d_bias[l], sizeof(float) * co) != cudaSuccess) return bad(NST_ERR_OOM);
     cudaMemcpy(ctx->d_bias[l], bl, sizeof(float) * co, cudaMemcpyHostToDevice);
     if (l == 0) {
+      // the BF16 form holds every weight, conv1_1's included, as a BF16 value (kept here as the
+      // float it converts to exactly); the FP32 form keeps them as given
+      std::vector<float> w1(Wl, Wl + (size_t)co * ci * 9);
+      if (ctx->bf16)
+        for (float &w : w1) w = bf2f(f2bf(w));
       for (int o = 0; o < co; o++) {
-        for (int k = 0; k < 27; k++) ctx->h_c11.w[k][o] = Wl[(size_t)o * 27 + k];
+        for (int k = 0; k < 27; k++) ctx->h_c11.w[k][o] = w1[(size_t)o * 27 + k];
         ctx->h_c11.b[o] = bl[o];
       }
       if (cudaMalloc(&ctx->d_w11, sizeof(float) * co * ci * 9) != cudaSuccess)
         return bad(NST_ERR_OOM);
-      cudaMemcpy(ctx->d_w11, Wl, sizeof(float) * co * ci * 9, cudaMemcpyHostToDevice);
+      cudaMemcpy(ctx->d_w11, w1.data(), sizeof(float) * co * ci * 9, cudaMemcpyHostToDevice);
       continue;
     }
     const size_t n = (size_t)co * ci * 9;

@@ -59,12 +59,25 @@ class GramLoss(torch.autograd.Function):
         return g * (R @ V), None, None, None
 
 
+class RoundPair(torch.autograd.Function):
+    """The BF16 form's image: hi = bf16(x), lo = bf16(x - hi); straight-through backward."""
+
+    @staticmethod
+    def forward(ctx, x):
+        hi = _q(x, "bf16")
+        return hi + _q(x - hi, "bf16")
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
 def torch_loss_storage(params, x, ct, grams, ws, lam, mode):
-    h = x[None]
+    h = (RoundPair.apply(x) if mode == "bf16" else x)[None]
     feats = {}
     for l, (w, b) in enumerate(params):
         W = torch.as_tensor(w, dtype=torch.float64)
-        if mode == "bf16" and l > 0:
+        if mode == "bf16":
             W = _q(W, mode)
         pre = F.conv2d(h, W, torch.as_tensor(b, dtype=torch.float64), padding=1)
         h = RoundAct.apply(F.relu(RoundGrad.apply(pre, mode)), mode)

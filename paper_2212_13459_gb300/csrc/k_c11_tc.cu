@@ -61,9 +61,21 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
   const uint32_t b_base = smem_base, a_base = smem_base + kFwdB;
+  __shared__ __align__(16) float bias_sh[64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long npix = (long long)B * Hb * Wb;
-  const int ntiles = (int)((npix + 127) / 128);
+  const int npix = B * Hb * Wb;   // < 2^31 (checked by the launcher)
+  const int ntiles = (npix + 127) / 128;
+  // pixel p0 + r of the flattened [B][Hb][Wb] buffer -> (b, y, x), from p0's coordinates
+  auto locate = [&](int p0, int r, int &b, int &y, int &x) {
+    const unsigned q = (unsigned)p0 / (unsigned)Wb;
+    x = p0 - (int)q * Wb + r;
+    y = (int)(q % (unsigned)Hb);
+    b = (int)(q / (unsigned)Hb);
+    while (x >= Wb) {
+      x -= Wb;
+      if (++y == Hb) { y = 0; ++b; }
+    }
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kFwdStages; s++) {
@@ -90,6 +102,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
         make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
                    pack_bf16x2(v[6], v[7]));
   }
+  if (threadIdx.x < 64) bias_sh[threadIdx.x] = bias[threadIdx.x];
   fence_proxy_async_smem();
   if (warp == 8) tmem_alloc(smem_u32(&tmem_base_sh), 128);
   tc_fence_before();
@@ -102,14 +115,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     const int row = threadIdx.x;
     const size_t plane = (size_t)H * W;
     auto gather = [&](int t, float *in) {
-      const long long p = (long long)t * 128 + row;
-      bool live = p < npix;
+      bool live = t * 128 + row < npix;
       int x = 0, y = 0, b = 0;
-      if (live) {
-        x = (int)(p % Wb);
-        y = (int)((p / Wb) % Hb);
-        b = (int)(p / ((long long)Wb * Hb));
-      }
+      if (live) locate(t * 128, row, b, y, x);
       const BlockGeom g = geom[live ? b : 0];
       live = live && y < g.eh && x < g.ew;
 #pragma unroll
@@ -174,20 +182,21 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       tmem_ld32(tb + 32, v + 32);
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
-      const long long p = (long long)t * 128 + row;
+      const int p = t * 128 + row;
       if (p < npix) {
-        const int x = (int)(p % Wb);
-        const int y = (int)((p / Wb) % Hb);
-        const int b = (int)(p / ((long long)Wb * Hb));
+        int b, y, x;
+        locate(t * 128, row, b, y, x);
         const BlockGeom g = geom[b];
         const bool valid = y < g.eh && x < g.ew;
         uint4 *o = reinterpret_cast<uint4 *>(out + (size_t)p * 64);
 #pragma unroll
         for (int c = 0; c < 8; c++) {
+          const float4 b0 = *reinterpret_cast<const float4 *>(bias_sh + c * 8);
+          const float4 b1 = *reinterpret_cast<const float4 *>(bias_sh + c * 8 + 4);
+          const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
           float r[8];
 #pragma unroll
-          for (int j = 0; j < 8; j++)
-            r[j] = valid ? fmaxf(v[c * 8 + j] + __ldg(bias + c * 8 + j), 0.f) : 0.f;
+          for (int j = 0; j < 8; j++) r[j] = valid ? fmaxf(v[c * 8 + j] + bb[j], 0.f) : 0.f;
           o[c] = make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]),
                             pack_bf16x2(r[4], r[5]), pack_bf16x2(r[6], r[7]));
         }
@@ -428,7 +437,9 @@ cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w1
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const long long ntiles = ((long long)B * Hb * Wb + 127) / 128;
+  const long long npix = (long long)B * Hb * Wb;
+  if (npix >= (1LL << 31) - 128) return cudaErrorInvalidValue;
+  const long long ntiles = (npix + 127) / 128;
   if (ntiles <= 0) return cudaSuccess;
   const int grid = (int)std::min<long long>(ntiles, 2LL * tc_num_sms());
   conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(img, H, W, w11, bias, geom, B, Hb, Wb,

@@ -509,6 +509,188 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---- pixels-as-N variant for 128-channel outputs ---------------------------------------------------
+// With Cout = 128 the natural tile (M = 128 pixels, N = 128 channels) issues MMAs half as wide as
+// the 256-channel layers, and a narrow MMA costs nearly as much issue time as a wide one. Here the
+// roles swap: M = the 128 output channels (A = a 128 x 64 weight box), N = 256 output pixels of a
+// TH x TW patch (B = the activation box), so every tcgen05.mma is 128 x 256 x 16 like the widest
+// layers. The accumulator holds D[channel][pixel]; each epilogue warp reads 32 channels x 32
+// pixels, transposes them through a private 4 KB shared-memory tile (16-byte chunks XOR-swizzled
+// by row, conflict-free both ways) and then runs the same per-pixel epilogue as the other kernels
+// (one pixel per lane, 32 consecutive channels).
+constexpr int kSwapBN = 128;                    // output channels per tile (M)
+constexpr int kSwapBP = 256;                    // output pixels per tile (N)
+constexpr uint32_t kSwapA = kSwapBN * kBK * 2;  // 16 KB weight box
+constexpr uint32_t kSwapB = kSwapBP * kBK * 2;  // 32 KB activation box
+constexpr uint32_t kSwapT = 32 * 32 * 4;        // transpose tile per epilogue warp
+
+template <int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_swap_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB,
+                        const __grid_constant__ CUtensorMap tmA2,
+                        const __grid_constant__ CUtensorMap tmB2, const ConvArgs a,
+                        const TcGeom tg) {
+  constexpr uint32_t STAGE_BYTES = kSwapA + kSwapB;
+  constexpr uint32_t TMEM_COLS = 2 * kSwapBP;
+  constexpr uint32_t IDESC = make_idesc(kSwapBP);
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(smem_u32(&tfull_bar[i]), 1);
+      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+  const int kb_total = tg.kb_main + tg.kb2;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: weight box (A) + activation box (B) per K-block ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
+        const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
+        const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
+        const int b = mt / (tg.tiles_x * tg.tiles_y);
+        const int x0 = tx * tg.TW, y0 = ty * tg.TH, n0 = nt * kSwapBN;
+        for (int kb = 0; kb < kb_total; kb++) {
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          const uint32_t sw = smem_base + stage * STAGE_BYTES, sx = sw + kSwapA;
+          mbar_expect_tx(fb, STAGE_BYTES);
+          if (kb < tg.kb_main) {
+            const int tap = kb / tg.cin_blocks, cb = kb % tg.cin_blocks;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            tma_load_2d(sw, &tmB, fb, tap * a.cin + cb * kBK, n0);
+            tma_load_4d(sx, &tmA, fb, cb * kBK, x0 + dx, y0 + dy, b);
+          } else {
+            const int cb = kb - tg.kb_main;
+            tma_load_2d(sw, &tmB2, fb, cb * kBK, n0);
+            tma_load_4d(sx, &tmA2, fb, cb * kBK, x0, y0, b);
+          }
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: D[128 ch][256 px] += W[128 x 64] X[256 x 64]^T ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x, it++) {
+        const int acc = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(acc * kSwapBP);
+        for (int kb = 0; kb < kb_total; kb++) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sw = smem_base + stage * STAGE_BYTES, sx = sw + kSwapA;
+          const uint64_t dw = sw128_desc(sw), dx = sw128_desc(sx);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; k++)
+            mma_bf16(d, dw + (uint64_t)(k * 2), dx + (uint64_t)(k * 2), IDESC,
+                     (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty_bar[stage]));
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (ok) mma_commit(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..9) ----------------
+    const int q = warp & 3;            // TMEM lane quarter = channels q*32 .. q*32+31 of the tile
+    const int half = (warp - 2) >> 2;  // pixels half*128 .. half*128+127 of the patch
+    uint8_t *tsm = smem_gen + STAGES * STAGE_BYTES + (size_t)(warp - 2) * kSwapT;
+    int it = 0;
+    for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
+      const int acc = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      tc_fence_after();
+      const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
+      const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
+      const int b = mt / (tg.tiles_x * tg.tiles_y);
+      const BlockGeom g = a.geom[b];
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kSwapBP);
+      const int n = nt * kSwapBN + q * 32;
+#pragma unroll 1
+      for (int c = half * (kSwapBP / 2); c < (half + 1) * (kSwapBP / 2); c += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c, v);   // v[j] = D[channel n + lane][pixel c + j]
+        // transpose: row j of the tile = pixel c + j, 16-byte chunk (lane / 4) ^ (j % 8)
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+          *reinterpret_cast<float *>(tsm + j * 128 + ((((lane >> 2) ^ (j & 7)) << 4) |
+                                                      ((lane & 3) << 2))) = v[j];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const float4 f = *reinterpret_cast<const float4 *>(tsm + lane * 128 +
+                                                             ((k ^ (lane & 7)) << 4));
+          v[4 * k] = f.x;
+          v[4 * k + 1] = f.y;
+          v[4 * k + 2] = f.z;
+          v[4 * k + 3] = f.w;
+        }
+        __syncwarp();
+        const int pp = c + lane;   // this lane's pixel of the patch, channels n .. n+31 in v
+        const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
+        const bool inb = y < a.Hb && x < a.Wb;
+        if (inb) epilogue32(a, g, b, y, x, n, v);
+        if (a.pool_out) {
+          if (!inb) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = 0.f;
+          }
+          pool_epilogue32(a, g, b, y, x, n, tg.TW, v);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty_bar[acc]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
 // ---- host side -------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -579,6 +761,37 @@ cudaError_t launch_bn(const CUtensorMap &A, const CUtensorMap &B, const CUtensor
   const int grid = std::min(tg.total, g_num_sms);
   conv_tc_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
   return cudaGetLastError();
+}
+
+template <int STAGES>
+cudaError_t launch_swap(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
+                        const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
+                        cudaStream_t s) {
+  constexpr size_t smem = (size_t)STAGES * (kSwapA + kSwapB) + 8 * kSwapT + 1024;
+  static_assert(smem <= 227 * 1024, "pixels-as-N kernel shared memory");
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_swap_kernel<STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int grid = std::min(tg.total, g_num_sms);
+  conv_tc_swap_kernel<STAGES><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
+  return cudaGetLastError();
+}
+
+// 256-pixel patch (TH * TW = 256) with the least padding; with fused pooling the rows of each
+// 32-pixel epilogue chunk must pair up (TW = 8 or 16)
+void pick_patch256(int H, int W, int &TH, int &TW, bool pool) {
+  static const int cand[6][2] = {{1, 256}, {2, 128}, {4, 64}, {8, 32}, {16, 16}, {32, 8}};
+  long long best = -1;
+  for (auto &c : cand) {
+    if (pool && c[1] > 16) continue;
+    const long long area = (long long)((H + c[0] - 1) / c[0]) * c[0] * ((W + c[1] - 1) / c[1]) *
+                           c[1];
+    if (best < 0 || area < best) { best = area; TH = c[0]; TW = c[1]; }
+  }
 }
 
 // output patch shape with the least padding over an H x W map (TH * TW = 128); with fused
@@ -690,9 +903,14 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   int hBN, hKB, hP2, hNT;
   if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
-  const int BN = a.cout >= 256 ? 256 : a.cout;
+  // 128 output channels: pixels as the MMA's N (256 wide) instead of channels (128 wide)
+  const bool swap = a.cout == kSwapBN;
+  const int BN = swap ? kSwapBN : (a.cout >= 256 ? 256 : a.cout);
   TcGeom tg;
-  pick_patch(a.Hb, a.Wb, tg.TH, tg.TW, a.pool_out != nullptr);
+  if (swap)
+    pick_patch256(a.Hb, a.Wb, tg.TH, tg.TW, a.pool_out != nullptr);
+  else
+    pick_patch(a.Hb, a.Wb, tg.TH, tg.TW, a.pool_out != nullptr);
   tg.tiles_x = (a.Wb + tg.TW - 1) / tg.TW;
   tg.tiles_y = (a.Hb + tg.TH - 1) / tg.TH;
   tg.n_tiles = a.cout / BN;
@@ -712,6 +930,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   }
   if (!a.taps) { mA = mA2; mB = mB2; }
   if (!a.k2) { mA2 = mA; mB2 = mB; }
+  if (swap) return launch_swap<4>(mA, mB, mA2, mB2, a, tg, s);
   switch (BN) {
     case 64: return launch_bn<64, 8>(mA, mB, mA2, mB2, a, tg, s);
     case 128: return launch_bn<128, 6>(mA, mB, mA2, mB2, a, tg, s);

@@ -53,6 +53,11 @@ CASES = [  # B, H, W, cin, cout, k2, taps, mode
     (3, 37, 29, 64, 64, 0, 9, 1),
     (2, 21, 30, 128, 128, 0, 9, 0),
     (1, 33, 17, 128, 128, 128, 9, 1),
+    # 128 output channels outside the halo shapes: pixels-as-N kernel (256-pixel patches)
+    (2, 19, 45, 256, 128, 0, 9, 1),
+    (1, 23, 50, 256, 128, 0, 9, 0),
+    (2, 7, 9, 0, 128, 128, 0, 1),
+    (1, 70, 90, 128, 128, 128, 9, 1),
 ]
 
 

@@ -3,13 +3,12 @@
 // conv1_1 is the only convolution whose input is the image itself: 27 taps x channels per output
 // pixel, too few for the implicit-GEMM kernels. Both directions become small GEMMs here:
 //
-//  * forward (Algorithm 1, both steps): D[p][n] = sum_k A[p][k] B[n][k] over 128 consecutive
-//    buffer pixels p, with A the im2col rows of the block (zero outside its valid extent) built
-//    by four producer warps straight into the 128-byte-swizzled K-major layout, and B the 64 x 64
-//    weight tile. The image stays FP32-accurate: each input value enters as hi + lo, two BF16
-//    numbers (hi = bf16(x), lo = bf16(x - hi), within 2^-17 |x| of x), A's row holding
-//    [27 hi | 27 lo | 10 zero] against B's [27 w | 27 w | 10 zero]. The epilogue adds the bias,
-//    applies ReLU, zeroes pixels outside the block's valid extent and stores the BF16 row.
+//  * forward (Algorithm 1, both steps): the block images are first staged as 16-byte BF16
+//    pixels (hi_0..2, lo_0..2, 0, 0) with hi = bf16(x), lo = bf16(x - hi), so each image value
+//    enters within 2^-17 |x| of its FP32 value; then D[p][n] = sum_k A[p][k] B[n][k] over a
+//    16 x 8 output patch with K = 9 taps x 8, every tap a shifted view of one TMA halo box (see
+//    the kernel). The epilogue adds the bias, applies ReLU, zeroes pixels outside the block's
+//    valid extent and stores the BF16 row.
 //  * input gradient (last line of Algorithm 1): P[q][j] = sum_co g[q][co] Wt[j][co] with
 //    j = 3 tap + ci (27 of N = 32 columns), over an 18 x 14 box of the gated ReLU1_1 gradient
 //    loaded by TMA (zero outside the buffer); the epilogue forms
@@ -40,16 +39,67 @@ __device__ __forceinline__ uint32_t sw128_chunk(int r, int c) {
 // ------------------------------------------------------------------------------------------------
 // forward
 // ------------------------------------------------------------------------------------------------
-constexpr int kFwdThreads = 288;   // warps 0-3 im2col, 4-7 epilogue, 8 MMA + TMEM allocation
-constexpr int kFwdStages = 4;
-constexpr uint32_t kFwdTile = 128 * 128;   // 128 rows x 64 BF16
-constexpr uint32_t kFwdB = 64 * 128;       // 64 rows x 64 BF16
-constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdTile;
+// Step 1: the block image in the BF16 form, one 16-byte pixel per buffer pixel:
+// xs[b][y][x] = (hi_0, hi_1, hi_2, lo_0, lo_1, lo_2, 0, 0) inside the block's valid extent, zero
+// elsewhere (the block is a standalone image with zero padding).
+__global__ void __launch_bounds__(256) conv11_stage_kernel(const float *__restrict__ img, int H,
+                                                           int W, const BlockGeom *__restrict__ geom,
+                                                           int B, int Hb, int Wb,
+                                                           uint4 *__restrict__ xs) {
+  const int npix = B * Hb * Wb;
+  const size_t plane = (size_t)H * W;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const unsigned q = (unsigned)p / (unsigned)Wb;
+    const int x = p - (int)q * Wb, y = (int)(q % (unsigned)Hb), b = (int)(q / (unsigned)Hb);
+    const BlockGeom g = geom[b];
+    uint4 o = make_uint4(0u, 0u, 0u, 0u);
+    if (y < g.eh && x < g.ew) {
+      const size_t off = (size_t)(g.ey0 + y) * W + g.ex0 + x;
+      float hi[3], lo[3];
+#pragma unroll
+      for (int ci = 0; ci < 3; ci++) {
+        const float v = __ldg(img + ci * plane + off);
+        hi[ci] = __bfloat162float(__float2bfloat16_rn(v));
+        lo[ci] = v - hi[ci];   // exact in FP32; rounded to BF16 by the packing below
+      }
+      o = make_uint4(pack_bf16x2(hi[0], hi[1]), pack_bf16x2(hi[2], lo[0]),
+                     pack_bf16x2(lo[1], lo[2]), 0u);
+    }
+    xs[p] = o;
+  }
+}
+
+// Step 2: the convolution, D[p][n] = sum_k A[p][k] B[n][k] with M = a 16 x 8 output patch and
+// K = 9 taps x 8 values (hi, lo, 2 zeros) + 8 zero columns = 80. One TMA box of 18 x 10 staged
+// pixels (16 bytes each, no swizzle) feeds all taps: in the K-major no-swizzle layout a "core
+// matrix" is 8 rows x 16 bytes, so row i of the patch (8 pixels) is one core matrix at
+// 160-byte steps (SBO) and the two taps of one K = 16 instruction are two core matrices of the
+// same box whose distance is the instruction's LBO. Five instructions per tile: taps (0,1),
+// (2,3), (4,5), (6,7), (8, -) with zero weights in the last one's second half.
+constexpr int kFwdThreads = 192;   // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
+constexpr int kFwdStages = 8;
+constexpr int kFwdTH = 16, kFwdTW = 8, kFwdBoxH = kFwdTH + 2, kFwdBoxW = kFwdTW + 2;
+constexpr uint32_t kFwdBoxBytes = kFwdBoxH * kFwdBoxW * 16;   // 2,880
+constexpr uint32_t kFwdStage = 3072;                         // box + zeroed tail
+constexpr uint32_t kFwdB = 16384;                            // 5 x 2 KB used, rest zero
+constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdStage;
+
+__device__ __forceinline__ uint64_t desc_k_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version; layout type 0 = no swizzle
+  return d;
+}
+__host__ __device__ constexpr uint32_t fwd_tap_off(int tap) {   // byte offset of a tap in the box
+  return (uint32_t)(((tap / 3) * kFwdBoxW + tap % 3) * 16);
+}
 
 __global__ void __launch_bounds__(kFwdThreads, 2)
-    conv11_fwd_tc_kernel(const float *__restrict__ img, int H, int W,
-                         const float *__restrict__ w11, const float *__restrict__ bias,
-                         const BlockGeom *__restrict__ geom, int B, int Hb, int Wb,
+    conv11_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmX, const float *__restrict__ w11,
+                         const float *__restrict__ bias, const BlockGeom *__restrict__ geom,
+                         int B, int Hb, int Wb, int tiles_x, int tiles_y,
                          __nv_bfloat16 *__restrict__ out, unsigned *err) {
   constexpr uint32_t IDESC = idesc_bf16_m128(64);
   extern __shared__ uint8_t smem_raw[];
@@ -57,29 +107,17 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
+  __shared__ __align__(16) float bias_sh[64];
 
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
   const uint32_t b_base = smem_base, a_base = smem_base + kFwdB;
-  __shared__ __align__(16) float bias_sh[64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int npix = B * Hb * Wb;   // < 2^31 (checked by the launcher)
-  const int ntiles = (npix + 127) / 128;
-  // pixel p0 + r of the flattened [B][Hb][Wb] buffer -> (b, y, x), from p0's coordinates
-  auto locate = [&](int p0, int r, int &b, int &y, int &x) {
-    const unsigned q = (unsigned)p0 / (unsigned)Wb;
-    x = p0 - (int)q * Wb + r;
-    y = (int)(q % (unsigned)Hb);
-    b = (int)(q / (unsigned)Hb);
-    while (x >= Wb) {
-      x -= Wb;
-      if (++y == Hb) { y = 0; ++b; }
-    }
-  };
+  const int ntiles = B * tiles_x * tiles_y;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kFwdStages; s++) {
-      mbar_init(smem_u32(&full_bar[s]), 128);
+      mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int i = 0; i < 2; i++) {
@@ -89,87 +127,80 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B tile: row n = output channel, K = [w(27) | w(27) | 0(10)], w = W1[n][ci][ky][kx]
-  for (int i = threadIdx.x; i < 64 * 8; i += kFwdThreads) {
-    const int n = i >> 3, c = i & 7;
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int k = c * 8 + j;
-      v[j] = k < 27 ? w11[n * 27 + k] : (k < 54 ? w11[n * 27 + k - 27] : 0.f);
+  // B: instruction i's 64 x 16 block at i * 2048: K half h (tap 2i + h) at + h * 1024, output
+  // channel n at + n * 16, holding (w[n][0][tap], w[n][1][tap], w[n][2][tap]) twice (for hi and
+  // lo) and two zeros; everything else zero. The stage tails past each box are zeroed too, so the
+  // K padding of the last instruction multiplies finite values by zero weights.
+  for (int i = threadIdx.x; i < (int)(kFwdB / 16); i += kFwdThreads) {
+    const int ins = i >> 7, h = (i >> 6) & 1, n = i & 63;
+    const int tap = 2 * ins + h;
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+    if (ins < 5 && tap < 9) {
+      w0 = w11[n * 27 + tap];
+      w1 = w11[n * 27 + 9 + tap];
+      w2 = w11[n * 27 + 18 + tap];
     }
-    *reinterpret_cast<uint4 *>(smem_gen + sw128_chunk(n, c)) =
-        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                   pack_bf16x2(v[6], v[7]));
+    *reinterpret_cast<uint4 *>(smem_gen + (size_t)i * 16) =
+        make_uint4(pack_bf16x2(w0, w1), pack_bf16x2(w2, w0), pack_bf16x2(w1, w2), 0u);
+  }
+  for (int i = threadIdx.x; i < kFwdStages * (int)((kFwdStage - kFwdBoxBytes) / 16);
+       i += kFwdThreads) {
+    const int st = i / (int)((kFwdStage - kFwdBoxBytes) / 16);
+    const int k = i % (int)((kFwdStage - kFwdBoxBytes) / 16);
+    *reinterpret_cast<uint4 *>(smem_gen + kFwdB + (size_t)st * kFwdStage + kFwdBoxBytes + k * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
   }
   if (threadIdx.x < 64) bias_sh[threadIdx.x] = bias[threadIdx.x];
   fence_proxy_async_smem();
-  if (warp == 8) tmem_alloc(smem_u32(&tmem_base_sh), 128);
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 128);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_base_sh;
 
-  if (warp < 4) {
-    // ---------------- im2col producer: one pixel (row) per thread ----------------
-    const int row = threadIdx.x;
-    const size_t plane = (size_t)H * W;
-    auto gather = [&](int t, float *in) {
-      bool live = t * 128 + row < npix;
-      int x = 0, y = 0, b = 0;
-      if (live) locate(t * 128, row, b, y, x);
-      const BlockGeom g = geom[live ? b : 0];
-      live = live && y < g.eh && x < g.ew;
-#pragma unroll
-      for (int ky = 0; ky < 3; ky++)
-#pragma unroll
-        for (int kx = 0; kx < 3; kx++) {
-          const int yy = y + ky - 1, xx = x + kx - 1;
-          const bool ok = live && yy >= 0 && yy < g.eh && xx >= 0 && xx < g.ew;
-          const size_t o = ok ? (size_t)(g.ey0 + yy) * W + g.ex0 + xx : 0;
-#pragma unroll
-          for (int ci = 0; ci < 3; ci++)
-            in[ci * 9 + ky * 3 + kx] = ok ? __ldg(img + ci * plane + o) : 0.f;
-        }
-    };
-    float cur[27], nxt[27];
-    int it = 0;
-    int t = blockIdx.x;
-    if (t < ntiles) gather(t, cur);
-    for (; t < ntiles; t += gridDim.x, it++) {
-      const int stage = it % kFwdStages;
-      const uint32_t phase = (uint32_t)(it / kFwdStages) & 1u;
-      const int tn = t + gridDim.x;
-      if (tn < ntiles) gather(tn, nxt);   // next tile's loads in flight while this one is stored
-      if (!mbar_wait_sleep(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, err)) break;
-      float hi[27], lo[27];
-#pragma unroll
-      for (int k = 0; k < 27; k++) {
-        hi[k] = __bfloat162float(__float2bfloat16_rn(cur[k]));
-        lo[k] = cur[k] - hi[k];   // exact in FP32
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        const int stage = it % kFwdStages;
+        const uint32_t phase = (uint32_t)(it / kFwdStages) & 1u;
+        const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
+        if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, err)) break;
+        const uint32_t fb = smem_u32(&full_bar[stage]);
+        mbar_expect_tx(fb, kFwdBoxBytes);
+        tma_load_4d(a_base + stage * kFwdStage, &tmX, fb, 0, tx * kFwdTW - 1, ty * kFwdTH - 1, b);
       }
-      uint8_t *arow = smem_gen + kFwdB + (size_t)stage * kFwdTile;
-#pragma unroll
-      for (int c = 0; c < 8; c++) {
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-          const int k = c * 8 + j;
-          v[j] = k < 27 ? hi[k] : (k < 54 ? lo[k - 27] : 0.f);
-        }
-        *reinterpret_cast<uint4 *>(arow + sw128_chunk(row, c)) =
-            make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                       pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-      }
-      fence_proxy_async_smem();
-      mbar_arrive(smem_u32(&full_bar[stage]));
-#pragma unroll
-      for (int k = 0; k < 27; k++) cur[k] = nxt[k];
     }
-  } else if (warp < 8) {
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+        const int stage = it % kFwdStages;
+        const uint32_t phase = (uint32_t)(it / kFwdStages) & 1u;
+        const int acc = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1u) ^ 1u, &abort_flag, err)) break;
+        tc_fence_after();
+        if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t sa = a_base + stage * kFwdStage;
+        const uint32_t d = tmem_base + (uint32_t)(acc * 64);
+#pragma unroll
+        for (int ins = 0; ins < 5; ins++) {
+          const uint32_t o0 = fwd_tap_off(2 * ins);
+          const uint32_t lbo = ins < 4 ? fwd_tap_off(2 * ins + 1) - o0 : 16u;
+          mma_bf16(d, desc_k_none(sa + o0, lbo, kFwdBoxW * 16),
+                   desc_k_none(b_base + ins * 2048, 1024, 128), IDESC, ins > 0 ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&empty_bar[stage]));
+        mma_commit(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
     // ---------------- epilogue: bias, ReLU, valid-extent mask, BF16 row store ----------------
     const int q = warp & 3;
-    const int row = q * 32 + lane;
+    const int row = q * 32 + lane;   // patch pixel (row / 8, row % 8)
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
       const int acc = it & 1;
@@ -182,13 +213,12 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       tmem_ld32(tb + 32, v + 32);
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
-      const int p = t * 128 + row;
-      if (p < npix) {
-        int b, y, x;
-        locate(t * 128, row, b, y, x);
+      const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
+      const int y = ty * kFwdTH + row / kFwdTW, x = tx * kFwdTW + row % kFwdTW;
+      if (y < Hb && x < Wb) {
         const BlockGeom g = geom[b];
         const bool valid = y < g.eh && x < g.ew;
-        uint4 *o = reinterpret_cast<uint4 *>(out + (size_t)p * 64);
+        uint4 *o = reinterpret_cast<uint4 *>(out + (((size_t)b * Hb + y) * Wb + x) * 64);
 #pragma unroll
         for (int c = 0; c < 8; c++) {
           const float4 b0 = *reinterpret_cast<const float4 *>(bias_sh + c * 8);
@@ -202,30 +232,10 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
         }
       }
     }
-  } else if (lane == 0) {
-    // ---------------- MMA issuer ----------------
-    int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
-      const int stage = it % kFwdStages;
-      const uint32_t phase = (uint32_t)(it / kFwdStages) & 1u;
-      const int acc = it & 1;
-      const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1u) ^ 1u, &abort_flag, err)) break;
-      tc_fence_after();
-      if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, err)) break;
-      tc_fence_after();
-      const uint64_t da = sw128_desc(a_base + stage * kFwdTile), db = sw128_desc(b_base);
-      const uint32_t d = tmem_base + (uint32_t)(acc * 64);
-#pragma unroll
-      for (int k = 0; k < 4; k++)
-        mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, k > 0 ? 1u : 0u);
-      mma_commit(smem_u32(&empty_bar[stage]));
-      mma_commit(smem_u32(&tfull_bar[acc]));
-    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, 128);
   }
@@ -428,7 +438,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w11,
                                  const float *bias, const BlockGeom *geom, int B, int Hb, int Wb,
-                                 __nv_bfloat16 *out, unsigned *err, cudaStream_t s) {
+                                 void *stage_buf, __nv_bfloat16 *out, unsigned *err,
+                                 cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(conv11_fwd_tc_kernel,
@@ -438,12 +449,28 @@ cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w1
     attr = true;
   }
   const long long npix = (long long)B * Hb * Wb;
-  if (npix >= (1LL << 31) - 128) return cudaErrorInvalidValue;
-  const long long ntiles = (npix + 127) / 128;
-  if (ntiles <= 0) return cudaSuccess;
+  if (npix >= (1LL << 31)) return cudaErrorInvalidValue;
+  if (npix <= 0) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(stage_buf) % 16) return cudaErrorInvalidValue;
+  const int sgrid = (int)std::min<long long>((npix + 255) / 256, 32LL * tc_num_sms());
+  conv11_stage_kernel<<<sgrid, 256, 0, s>>>(img, H, W, geom, B, Hb, Wb,
+                                            reinterpret_cast<uint4 *>(stage_buf));
+  EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(tc_encode_tiled_fn());
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap m;
+  cuuint64_t dims[4] = {8, (cuuint64_t)Wb, (cuuint64_t)Hb, (cuuint64_t)B};
+  cuuint64_t strides[3] = {16, (cuuint64_t)Wb * 16, (cuuint64_t)Hb * Wb * 16};
+  cuuint32_t box[4] = {8, kFwdBoxW, kFwdBoxH, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, stage_buf, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int tiles_x = (Wb + kFwdTW - 1) / kFwdTW, tiles_y = (Hb + kFwdTH - 1) / kFwdTH;
+  const long long ntiles = (long long)B * tiles_x * tiles_y;
   const int grid = (int)std::min<long long>(ntiles, 2LL * tc_num_sms());
-  conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(img, H, W, w11, bias, geom, B, Hb, Wb,
-                                                           out, err);
+  conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(m, w11, bias, geom, B, Hb, Wb, tiles_x,
+                                                           tiles_y, out, err);
   return cudaGetLastError();
 }
 

@@ -855,9 +855,8 @@ bool halo_shape(const ConvArgs &a, int *BN, int *KB, int *P2KB, int *NT) {
   if (a.cin == 64 && a.cout == 64 && a.k2 <= 64) { *BN = 64; *NT = 1; return true; }
   if (a.cin == 64 && a.cout == 128 && a.k2 == 0) { *BN = 128; *NT = 1; return true; }
   if (a.cin == 128 && a.cout == 64 && a.k2 == 0) { *BN = 64; *NT = 1; return true; }
-  // (the input gradient of conv2_2, k2 = 128, is faster on the main kernel: two N slices each
-  // re-read the boxes of both operands)
-  if (a.cin == 128 && a.cout == 128 && a.k2 == 0) { *BN = 64; *NT = 2; return true; }
+  // (conv2_2, 128 -> 128, runs faster on the pixels-as-N kernel with 256-wide MMAs than here
+  // with two 64-wide N slices; conv2_1, 64 -> 128, is faster here)
   return false;
 }
 
@@ -878,8 +877,6 @@ cudaError_t launch_conv_tc_halo(const ConvArgs &a, int BN, int KB, int P2KB, int
   if (BN == 64 && KB == 1 && P2KB == 1 && NT == 1) return launch_halo<64, 1, 1, 1>(mA, mB, mA2, mB2, a, s);
   if (BN == 128 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<128, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
   if (BN == 64 && KB == 2 && P2KB == 0 && NT == 1) return launch_halo<64, 2, 0, 1>(mA, mB, mA2, mB2, a, s);
-  if (BN == 64 && KB == 2 && P2KB == 0 && NT == 2) return launch_halo<64, 2, 0, 2>(mA, mB, mA2, mB2, a, s);
-  if (BN == 64 && KB == 2 && P2KB == 2 && NT == 2) return launch_halo<64, 2, 2, 2>(mA, mB, mA2, mB2, a, s);
   return cudaErrorInvalidValue;
 }
 

@@ -469,8 +469,10 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
     Timer tm(ctx, kTOther, s);
     ctx->launches++;
     if (ctx->use_tc) {
+      // the staged BF16-pair image goes to the (not yet used) second gradient buffer
       cudaError_t e = launch_conv11_fwd_tc(img, p.H, p.W, ctx->d_w11, ctx->d_bias[0], geom, bt.B,
-                                           p.Hb, p.Wb, (__nv_bfloat16 *)ws.act[0], ctx->d_err, s);
+                                           p.Hb, p.Wb, ws.g[1], (__nv_bfloat16 *)ws.act[0],
+                                           ctx->d_err, s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "conv1_1 tensor-core forward launch");
     } else {
       launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);

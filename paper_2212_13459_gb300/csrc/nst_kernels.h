@@ -90,11 +90,13 @@ int tc_num_sms();
 
 // k_c11_tc.cu: conv1_1 on the tensor cores (BF16 storage). Forward: out[b][y][x][64] =
 // relu(bias + conv1_1(block image)) inside each block's valid extent, zero elsewhere; w11 is
-// [64][3][3][3] FP32 holding BF16 values. Input gradient: grad[ci][ey0 + y][ex0 + x] for the
-// owned (inner) pixels of every block, from the gated ReLU1_1 gradient g [B][Hb][Wb][64].
+// [64][3][3][3] FP32 holding BF16 values; stage_buf (16 bytes per buffer pixel, 16-byte aligned)
+// receives the staged block images. Input gradient: grad[ci][ey0 + y][ex0 + x] for the owned
+// (inner) pixels of every block, from the gated ReLU1_1 gradient g [B][Hb][Wb][64].
 cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w11,
                                  const float *bias, const BlockGeom *geom, int B, int Hb, int Wb,
-                                 __nv_bfloat16 *out, unsigned *err, cudaStream_t s);
+                                 void *stage_buf, __nv_bfloat16 *out, unsigned *err,
+                                 cudaStream_t s);
 cudaError_t launch_conv11_dgrad_tc(const __nv_bfloat16 *g, const float *w11,
                                    const BlockGeom *geom, const OwnRect *inner, int B, int Hb,
                                    int Wb, int max_inner_h, int max_inner_w, float *grad, int H,

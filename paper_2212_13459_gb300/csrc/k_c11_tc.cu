@@ -82,7 +82,8 @@ constexpr int kFwdTH = 16, kFwdTW = 8, kFwdBoxH = kFwdTH + 2, kFwdBoxW = kFwdTW 
 constexpr uint32_t kFwdBoxBytes = kFwdBoxH * kFwdBoxW * 16;   // 2,880
 constexpr uint32_t kFwdStage = 3072;                         // box + zeroed tail
 constexpr uint32_t kFwdB = 16384;                            // 5 x 2 KB used, rest zero
-constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdStage;
+constexpr uint32_t kFwdOut = 128 * 128;                      // one output tile, 128-B swizzle
+constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdStage + 2 * kFwdOut;
 
 __device__ __forceinline__ uint64_t desc_k_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -97,10 +98,10 @@ __host__ __device__ constexpr uint32_t fwd_tap_off(int tap) {   // byte offset o
 }
 
 __global__ void __launch_bounds__(kFwdThreads, 2)
-    conv11_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmX, const float *__restrict__ w11,
+    conv11_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                         const __grid_constant__ CUtensorMap tmO, const float *__restrict__ w11,
                          const float *__restrict__ bias, const BlockGeom *__restrict__ geom,
-                         int B, int Hb, int Wb, int tiles_x, int tiles_y,
-                         __nv_bfloat16 *__restrict__ out, unsigned *err) {
+                         int B, int Hb, int Wb, int tiles_x, int tiles_y, unsigned *err) {
   constexpr uint32_t IDESC = idesc_bf16_m128(64);
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kFwdStages], empty_bar[kFwdStages];
@@ -108,10 +109,12 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   __shared__ __align__(16) float bias_sh[64];
+  __shared__ int epi_ok;
 
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
   const uint32_t b_base = smem_base, a_base = smem_base + kFwdB;
+  const uint32_t o_off = kFwdB + kFwdStages * kFwdStage;   // two output staging tiles
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = B * tiles_x * tiles_y;
 
@@ -198,14 +201,23 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       }
     }
   } else {
-    // ---------------- epilogue: bias, ReLU, valid-extent mask, BF16 row store ----------------
+    // ---------------- epilogue: bias, ReLU, valid-extent mask, BF16 tile -> TMA store ----------------
+    // Each thread writes its pixel's 128-byte row into a 128-byte-swizzled staging tile (chunk c
+    // of row r at c ^ (r & 7): conflict-free), and one thread stores the 16 x 8 x 64 tile with
+    // one TMA copy (full-line writes; rows / columns past the buffer are clipped). Two staging
+    // tiles alternate; a tile is rewritten only after its store has finished reading it.
     const int q = warp & 3;
     const int row = q * 32 + lane;   // patch pixel (row / 8, row % 8)
+    const int et = threadIdx.x - 64;
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1u, &abort_flag, err)) break;
+      // one thread waits (bounded) and broadcasts, so all 128 threads leave the loop together;
+      // the same barrier tells everyone that staging tile (it & 1) is free again
+      if (et == 0) epi_ok = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1u, &abort_flag, err);
+      named_bar_sync(1, 128);
+      if (!epi_ok) break;
       tc_fence_after();
       float v[64];
       const uint32_t tb = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 64);
@@ -215,23 +227,31 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       mbar_arrive(smem_u32(&tempty_bar[acc]));
       const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
       const int y = ty * kFwdTH + row / kFwdTW, x = tx * kFwdTW + row % kFwdTW;
-      if (y < Hb && x < Wb) {
-        const BlockGeom g = geom[b];
-        const bool valid = y < g.eh && x < g.ew;
-        uint4 *o = reinterpret_cast<uint4 *>(out + (((size_t)b * Hb + y) * Wb + x) * 64);
+      const BlockGeom g = geom[b];
+      const bool valid = y < g.eh && x < g.ew;
+      uint8_t *orow = smem_gen + o_off + (size_t)(it & 1) * kFwdOut + (size_t)row * 128;
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
-          const float4 b0 = *reinterpret_cast<const float4 *>(bias_sh + c * 8);
-          const float4 b1 = *reinterpret_cast<const float4 *>(bias_sh + c * 8 + 4);
-          const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-          float r[8];
+      for (int c = 0; c < 8; c++) {
+        const float4 b0 = *reinterpret_cast<const float4 *>(bias_sh + c * 8);
+        const float4 b1 = *reinterpret_cast<const float4 *>(bias_sh + c * 8 + 4);
+        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float r[8];
 #pragma unroll
-          for (int j = 0; j < 8; j++) r[j] = valid ? fmaxf(v[c * 8 + j] + bb[j], 0.f) : 0.f;
-          o[c] = make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]),
-                            pack_bf16x2(r[4], r[5]), pack_bf16x2(r[6], r[7]));
-        }
+        for (int j = 0; j < 8; j++) r[j] = valid ? fmaxf(v[c * 8 + j] + bb[j], 0.f) : 0.f;
+        *reinterpret_cast<uint4 *>(orow + ((c ^ (row & 7)) << 4)) =
+            make_uint4(pack_bf16x2(r[0], r[1]), pack_bf16x2(r[2], r[3]),
+                       pack_bf16x2(r[4], r[5]), pack_bf16x2(r[6], r[7]));
+      }
+      fence_proxy_async_smem();
+      named_bar_sync(1, 128);
+      if (et == 0) {
+        tma_store_4d(&tmO, smem_base + o_off + (uint32_t)(it & 1) * kFwdOut, 0, tx * kFwdTW,
+                     ty * kFwdTH, b);
+        bulk_commit();
+        bulk_wait_read_1();
       }
     }
+    if (et == 0) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();
@@ -466,11 +486,19 @@ cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w1
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  CUtensorMap mo;
+  cuuint64_t odims[4] = {64, (cuuint64_t)Wb, (cuuint64_t)Hb, (cuuint64_t)B};
+  cuuint64_t ostrides[3] = {128, (cuuint64_t)Wb * 128, (cuuint64_t)Hb * Wb * 128};
+  cuuint32_t obox[4] = {64, kFwdTW, kFwdTH, 1};
+  r = enc(&mo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, out, odims, ostrides, obox, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const int tiles_x = (Wb + kFwdTW - 1) / kFwdTW, tiles_y = (Hb + kFwdTH - 1) / kFwdTH;
   const long long ntiles = (long long)B * tiles_x * tiles_y;
   const int grid = (int)std::min<long long>(ntiles, 2LL * tc_num_sms());
-  conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(m, w11, bias, geom, B, Hb, Wb, tiles_x,
-                                                           tiles_y, out, err);
+  conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(m, mo, w11, bias, geom, B, Hb, Wb,
+                                                           tiles_x, tiles_y, err);
   return cudaGetLastError();
 }
 

@@ -276,16 +276,19 @@ def e2e_leg(ctx, x, H, W, args, dist, dev, world):
 
 
 def lbfgs_leg(x, grad, H, W, stream, dev):
-    """One L-BFGS iteration (driver step, history 10) on the workload's image size, on the
-    quadratic model E = |x - x0|^2 / 2 (g = x - x0) so that every pair is stored."""
+    """One L-BFGS iteration (driver step, history 10) on the workload's image size, timed with
+    a full history: the quadratic model E = sum_i d_i (x_i - x0_i)^2 / 2 with curvatures d_i
+    spread over [0.01, 1], so every pair is stored and the history stays full."""
     import torch
     from paper_2212_13459_gb300 import native
     opt = native.LBFGS(3 * H * W, 10)
     xl = x + 0.01 * grad
+    gen = torch.Generator(device=dev).manual_seed(0)
+    dcurv = torch.pow(10.0, -2.0 * torch.rand(x.shape, device=dev, generator=gen))
     g = torch.empty_like(x)
     total = 0.0
     for k in range(17):
-        torch.sub(xl, x, out=g)
+        torch.mul(xl - x, dcurv, out=g)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         opt.step(xl, g)

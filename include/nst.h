@@ -143,14 +143,16 @@ const char *nst_last_error(nst_ctx *ctx);
 nst_status nst_tile_plan(int H, int W, int tiles_h, int tiles_w, int margin, int *rects_out);
 
 /* ---- L-BFGS (Section 3.1; history sizes of Section 5.1) --------------------------------------
- * Two-loop recursion over the m newest pairs, H0 = gamma I with gamma = s^T y / y^T y, pairs
- * with y^T s <= 1e-10 skipped, no line search: step 1 except min(1, 1/||g||_1) on the first
- * iteration. FP32 vectors, FP64 dot products, all on the device (no host round trip).
- * State (history 2 m n floats) is owned by the nst_lbfgs object, allocated at create. */
+ * The inverse-BFGS matrix of the m newest pairs (the matrix the two-loop recursion applies),
+ * H0 = gamma I with gamma = s^T y / y^T y of the newest pair, pairs with y^T s <= 1e-10 skipped,
+ * no line search: step 1 except min(1, 1/||g||_1) on the first iteration. Applied in its compact
+ * form (two passes over the stored vectors per step). FP32 vectors, dot products summed in FP64
+ * in a fixed order, all on the device (no host round trip). State (history 2 (m + 1) n floats)
+ * is owned by the nst_lbfgs object, allocated at create. */
 nst_status nst_lbfgs_create(nst_lbfgs **out, long long n, int m);
 /* As nst_lbfgs_create, with flags. NST_LBFGS_HOST_HISTORY keeps the 2 (m + 1) history vectors in
  * page-locked host memory mapped into the device address space (on a Grace-Blackwell node the
- * two-loop kernels read them over NVLink-C2C): the GPU analogue of the paper's moving the L-BFGS
+ * step's kernels read them over NVLink-C2C): the GPU analogue of the paper's moving the L-BFGS
  * history to the CPU at the last scale to free device memory (Section 5.1). Same results. */
 enum { NST_LBFGS_HOST_HISTORY = 1 };
 nst_status nst_lbfgs_create_ex(nst_lbfgs **out, long long n, int m, int flags);

@@ -1,8 +1,14 @@
 // k_lbfgs.cu -- HBM-bound vector kernels of the optimiser and of the multiscale initialisation:
-//   * L-BFGS two-loop recursion (Section 3.1, after Nocedal 1980): FP64 dot products with a
-//     deterministic two-stage reduction, axpy updates whose coefficients stay in device memory,
-//     and the step/update kernel. History slots are resolved on the device, so a step needs no
-//     host round trip.
+//   * the L-BFGS step (Section 3.1, after Nocedal 1980) in the compact representation of the
+//     inverse-BFGS matrix (Byrd, Nocedal and Schnabel 1994): with S, Y the stored pairs (oldest
+//     first), R the upper triangle of S^T Y, D its diagonal and H0 = gamma I,
+//         H g = gamma g + S p - gamma Y u,  u = R^-1 (S^T g),
+//                                           p = R^-T ((D + gamma Y^T Y) u - gamma Y^T g),
+//     the same matrix the two-loop recursion applies. A step reads every stored vector twice
+//     (one fused pass for all dot products, one pass forming the step) instead of four times;
+//     S^T Y and Y^T Y are kept up to date from the new pair's dot products. Dots are FP32 chunks
+//     summed in FP64 with fixed-order reductions; the small solve runs in FP64 on one thread.
+//     History slots are resolved on the device, so a step needs no host round trip.
 //   * bicubic x2 upscaling used to initialise each scale after the first (Algorithm 2).
 #include "nst_internal.cuh"
 #include "nst_kernels.h"
@@ -10,183 +16,245 @@
 
 namespace nst {
 
-constexpr int kDotBlocks = 1216;   // 8 CTAs per SM on 152 SMs; fixed so reductions are reproducible
 constexpr int kDotThreads = 256;
-int dot_partials_count() { return kDotBlocks; }
+constexpr int kDotBlocksTotal = 1216;   // 8 CTAs per SM on 152 SMs, shared among the groups
 
-__device__ __forceinline__ const float *resolve(const VecRef &r) {
-  if (!r.slot) return r.base;
-  const int s = *r.slot;
-  return s < 0 ? nullptr : r.base + (size_t)s * r.stride;
+static int dot_groups(int m) { return (m + 1 + kLbGroup - 1) / kLbGroup; }
+static int dot_blocks(int m) {   // CTAs per group; fixed for a given m (reproducible reductions)
+  const int b = kDotBlocksTotal / dot_groups(m);
+  return b < 152 ? 152 : b;
 }
+int lbfgs_partials_count(int m) { return 4 * (m + 1) * dot_blocks(m); }
 
-// partial[blockIdx] = sum over the CTA's grid-stride share of a[i]*b[i] (or |a[i]|), in FP64
-__global__ void __launch_bounds__(kDotThreads) dot_partial_kernel(VecRef ra, VecRef rb,
-                                                                  long long n, int abs_mode,
-                                                                  double *__restrict__ partial) {
-  __shared__ double red[kDotThreads];
-  const float *a = resolve(ra);
-  const float *b = abs_mode ? nullptr : resolve(rb);
-  double s = 0.0;
-  if (a && (abs_mode || b)) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-      if (abs_mode)
-        s += fabs((double)a[i]);
-      else
-        s = fma((double)a[i], (double)b[i], s);
-    }
-  }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = kDotThreads / 2; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
-
-// *out = mul * sum(partial) in fixed order; mul = rho[*slot] (0 if the slot is empty) or 1.
-// In abs mode the result is the first step length min(1, 1 / sum).
-__global__ void __launch_bounds__(1024) dot_final_kernel(const double *__restrict__ partial, int np,
-                                                         const double *__restrict__ mul_base,
-                                                         const int *__restrict__ mul_slot,
-                                                         int abs_mode, double *__restrict__ out) {
-  __shared__ double red[1024];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = 512; k > 0; k >>= 1) {
-    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
-    __syncthreads();
-  }
+// Position p of the fused pass: p = 0 is the candidate pair (spare slot: last step s and the new
+// y), p = 1 .. count the stored pairs order[p - 1]. partials[(4 p + q) * nb + cta] for the dots
+// q = 0: s.g, 1: y.g, 2: s.y_new, 3: y.y_new.
+__global__ void __launch_bounds__(kDotThreads) lbfgs_dots_kernel(
+    const float *__restrict__ g, const float *__restrict__ g_prev, const float *__restrict__ S,
+    float *__restrict__ Y, long long stride, long long n, const LbfgsCtl *__restrict__ c,
+    int first, double *__restrict__ partials) {
+  constexpr int G = kLbGroup;
+  __shared__ int sl[G];
+  __shared__ int nj_sh, sp_sh;
+  __shared__ double red[kDotThreads / 32][4 * G];
+  const int grp = blockIdx.y, nb = gridDim.x;
   if (threadIdx.x == 0) {
-    double r = red[0];
-    if (abs_mode) {
-      r = r > 1.0 ? 1.0 / r : 1.0;
-    } else if (mul_base) {
-      const int sl = mul_slot ? *mul_slot : 0;
-      r = sl < 0 ? 0.0 : mul_base[sl] * r;
+    const int count = c->count;
+    int nj = 0;
+    for (int j = 0; j < G; j++) {
+      const int p = grp * G + j;
+      if (p <= count) {
+        sl[j] = p == 0 ? c->spare : c->order[p - 1];
+        nj = j + 1;
+      }
     }
-    *out = r;
+    nj_sh = first ? (grp == 0 ? 1 : 0) : nj;
+    sp_sh = c->spare;
+  }
+  __syncthreads();
+  const int nj = nj_sh;
+  if (nj == 0) return;
+  float *ynew = first ? nullptr : Y + (size_t)sp_sh * stride;
+  const long long step = (long long)nb * kDotThreads;
+  double acc[G][4];
+  float part[G][4];
+#pragma unroll
+  for (int j = 0; j < G; j++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc[j][q] = 0.0, part[j][q] = 0.f;
+  int chunk = 0;
+  for (long long i = (long long)blockIdx.x * kDotThreads + threadIdx.x; i < n; i += step) {
+    const float gv = g[i];
+    if (first) {
+      part[0][0] += fabsf(gv);
+    } else {
+      const float yv = gv - g_prev[i];
+      if (grp == 0) ynew[i] = yv;
+#pragma unroll
+      for (int j = 0; j < G; j++) {
+        if (j < nj) {
+          const size_t o = (size_t)sl[j] * stride + i;
+          const float sv = S[o];
+          const float wv = (grp == 0 && j == 0) ? yv : Y[o];
+          part[j][0] = fmaf(sv, gv, part[j][0]);
+          part[j][1] = fmaf(wv, gv, part[j][1]);
+          part[j][2] = fmaf(sv, yv, part[j][2]);
+          part[j][3] = fmaf(wv, yv, part[j][3]);
+        }
+      }
+    }
+    if (++chunk == 16) {   // FP32 over 16 elements, FP64 across chunks
+      chunk = 0;
+#pragma unroll
+      for (int j = 0; j < G; j++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[j][q] += (double)part[j][q], part[j][q] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < G; j++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc[j][q] += (double)part[j][q];
+  // fixed-order block reduction: warp shuffles, then the warps in index order
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < G; j++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      double v = acc[j][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][j * 4 + q] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < 4 * nj) {
+    double v = 0.0;
+    for (int w = 0; w < kDotThreads / 32; w++) v += red[w][threadIdx.x];
+    const int d = grp * G * 4 + threadIdx.x;   // = 4 p + q
+    partials[(size_t)d * nb + blockIdx.x] = v;
   }
 }
 
-void launch_dot_ref(const VecRef &a, const VecRef &b, long long n, double *partials, double *out,
-                    const double *mul_base, const int *mul_slot, int abs_mode, cudaStream_t s) {
-  dot_partial_kernel<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, n, abs_mode, partials);
-  dot_final_kernel<<<1, 1024, 0, s>>>(partials, kDotBlocks, mul_base, mul_slot, abs_mode, out);
+void launch_lbfgs_dots(const float *g, const float *g_prev, const float *S, float *Y,
+                       long long stride, long long n, const LbfgsCtl *c, int m, int first,
+                       double *partials, cudaStream_t s) {
+  dim3 grid(dot_blocks(m), first ? 1 : dot_groups(m));
+  lbfgs_dots_kernel<<<grid, kDotThreads, 0, s>>>(g, g_prev, S, Y, stride, n, c, first, partials);
 }
 
-// y += (c1 - c2) * x, with c1, c2 device scalars (c2 may be null) and x resolved on the device;
-// no-op when x's slot is empty
-__global__ void axpy_kernel(float *__restrict__ y, VecRef rx, long long n,
-                            const double *__restrict__ c1, const double *__restrict__ c2,
-                            float sign) {
-  const float *x = resolve(rx);
-  if (!x) return;
-  const float c = sign * (float)(*c1 - (c2 ? *c2 : 0.0));
-  // the float4 path needs both vectors 16-byte aligned; otherwise everything goes scalar
-  const bool vec = (((uintptr_t)y | (uintptr_t)x) & 15) == 0;
-  const long long n4 = vec ? n / 4 : 0;
-  float4 *y4 = reinterpret_cast<float4 *>(y);
-  const float4 *x4 = reinterpret_cast<const float4 *>(x);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-       i += (long long)gridDim.x * blockDim.x) {
-    float4 a = y4[i], b = x4[i];
-    a.x = fmaf(c, b.x, a.x);
-    a.y = fmaf(c, b.y, a.y);
-    a.z = fmaf(c, b.z, a.z);
-    a.w = fmaf(c, b.w, a.w);
-    y4[i] = a;
+__global__ void __launch_bounds__(256) lbfgs_solve_kernel(LbfgsCtl *__restrict__ c,
+                                                          const double *__restrict__ partials,
+                                                          int nb, int m, int first, double eps,
+                                                          double *__restrict__ SY,
+                                                          double *__restrict__ YY) {
+  __shared__ double dots[4 * (kMaxHistory + 1)];
+  __shared__ double sg[kMaxHistory + 1], yg[kMaxHistory + 1];   // by slot
+  __shared__ double u[kMaxHistory], w[kMaxHistory], pv[kMaxHistory];
+  __shared__ int sl[kMaxHistory];
+  const int count0 = c->count;
+  const int nd = first ? 1 : 4 * (count0 + 1);
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nb; b++) v += partials[(size_t)d * nb + b];   // fixed order
+    dots[d] = v;
   }
-  for (long long i = n4 * 4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] = fmaf(c, x[i], y[i]);
-}
-
-static int vec_grid(long long n) {
-  long long b = (n / 4 + 255) / 256;
-  return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
-}
-
-void launch_axpy_ref(float *y, const VecRef &x, long long n, const double *c1, const double *c2,
-                     float sign, cudaStream_t s) {
-  axpy_kernel<<<vec_grid(n), 256, 0, s>>>(y, x, n, c1, c2, sign);
-}
-
-// out = a - b, out resolved on the device (the spare history slot)
-__global__ void sub_kernel(VecRef rout, const float *__restrict__ a, const float *__restrict__ b,
-                           long long n) {
-  float *out = const_cast<float *>(resolve(rout));
-  if (!out) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = a[i] - b[i];
-}
-void launch_sub_ref(const VecRef &out, const float *a, const float *b, long long n,
-                    cudaStream_t s) {
-  sub_kernel<<<vec_grid(n * 4), 256, 0, s>>>(out, a, b, n);
-}
-
-// y = gamma * x (gamma device scalar)
-__global__ void scale_kernel(float *__restrict__ y, const float *__restrict__ x, long long n,
-                             const double *__restrict__ gamma) {
-  const float g = (float)*gamma;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    y[i] = g * x[i];
-}
-void launch_scale_dev(float *y, const float *x, long long n, const double *gamma,
-                      cudaStream_t s) {
-  scale_kernel<<<vec_grid(n * 4), 256, 0, s>>>(y, x, n, gamma);
-}
-
-// s = -t r stored in the spare slot; x += s; g_prev = g
-__global__ void lbfgs_finish_kernel(float *__restrict__ x, VecRef rs, float *__restrict__ g_prev,
-                                    const float *__restrict__ r, const float *__restrict__ g,
-                                    long long n, const double *__restrict__ t) {
-  float *sv = const_cast<float *>(resolve(rs));
-  const float tt = (float)*t;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float st = -tt * r[i];
-    if (sv) sv[i] = st;
-    x[i] += st;
-    g_prev[i] = g[i];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (first) {
+    const double l1 = dots[0];
+    c->k = 0;
+    c->cg = (float)-(l1 > 1.0 ? 1.0 / l1 : 1.0);   // t = min(1, 1 / ||g||_1), d = -g
+    return;
   }
-}
-void launch_lbfgs_finish_ref(float *x, const VecRef &s_next, float *g_prev, const float *r,
-                             const float *g, long long n, const double *t, cudaStream_t s) {
-  lbfgs_finish_kernel<<<vec_grid(n * 4), 256, 0, s>>>(x, s_next, g_prev, r, g, n, t);
-}
-
-// Curvature test and history bookkeeping, one thread. ys = y^T s, yy = y^T y of the pair held in
-// the spare slot. Accepted pairs go to the front of `order` (newest first); the slot dropped
-// from the back (if the history is full) or any slot not in `order` becomes the next spare.
-__global__ void lbfgs_accept_kernel(LbfgsCtl *__restrict__ c, double *__restrict__ rho, int m,
-                                    double eps) {
-  if (threadIdx.x || blockIdx.x) return;
-  const double ys = c->ys, yy = c->yy;
+  const int ld = m + 1;
   const int sp = c->spare;
+  sg[sp] = dots[0];
+  yg[sp] = dots[1];
+  for (int p = 1; p <= count0; p++) {
+    sg[c->order[p - 1]] = dots[4 * p];
+    yg[c->order[p - 1]] = dots[4 * p + 1];
+  }
+  const double ys = dots[2], yy = dots[3];
   if (ys > eps) {
-    rho[sp] = 1.0 / ys;
+    // the candidate becomes the newest pair: its column of S^T Y and row / column of Y^T Y
+    for (int p = 1; p <= count0; p++) {
+      const int a = c->order[p - 1];
+      SY[(size_t)a * ld + sp] = dots[4 * p + 2];
+      YY[(size_t)a * ld + sp] = dots[4 * p + 3];
+      YY[(size_t)sp * ld + a] = dots[4 * p + 3];
+    }
+    SY[(size_t)sp * ld + sp] = ys;
+    YY[(size_t)sp * ld + sp] = yy;
     c->gamma = ys / yy;
-    const int keep = c->count < m ? c->count : m - 1;
+    const int keep = count0 < m ? count0 : m - 1;
     for (int i = keep; i >= 1; i--) c->order[i] = c->order[i - 1];
     c->order[0] = sp;
     c->count = keep + 1;
     for (int i = c->count; i < m; i++) c->order[i] = -1;
-    for (int s = 0; s <= m; s++) {
+    for (int s = 0; s <= m; s++) {   // first slot not in use receives the next step
       bool used = false;
       for (int i = 0; i < c->count; i++) used |= c->order[i] == s;
       if (!used) { c->spare = s; break; }
     }
   }
+  const int k = c->count;
+  const double gamma = k > 0 ? c->gamma : 1.0;
+  for (int i = 0; i < k; i++) sl[i] = c->order[k - 1 - i];   // oldest first
+  // u = R^-1 (S^T g), R_ij = s_i . y_j (i <= j)
+  for (int i = k - 1; i >= 0; i--) {
+    double v = sg[sl[i]];
+    for (int j = i + 1; j < k; j++) v -= SY[(size_t)sl[i] * ld + sl[j]] * u[j];
+    u[i] = v / SY[(size_t)sl[i] * ld + sl[i]];
+  }
+  // w = (D + gamma Y^T Y) u - gamma Y^T g
+  for (int i = 0; i < k; i++) {
+    double v = 0.0;
+    for (int j = 0; j < k; j++) v += YY[(size_t)sl[i] * ld + sl[j]] * u[j];
+    w[i] = SY[(size_t)sl[i] * ld + sl[i]] * u[i] + gamma * (v - yg[sl[i]]);
+  }
+  // p = R^-T w
+  for (int i = 0; i < k; i++) {
+    double v = w[i];
+    for (int j = 0; j < i; j++) v -= SY[(size_t)sl[j] * ld + sl[i]] * pv[j];
+    pv[i] = v / SY[(size_t)sl[i] * ld + sl[i]];
+  }
+  // d = -H g = -gamma g - S p + gamma Y u; step length 1
+  c->k = k;
+  for (int i = 0; i < k; i++) {
+    c->slot[i] = sl[i];
+    c->cS[i] = (float)(-pv[i]);
+    c->cY[i] = (float)(gamma * u[i]);
+  }
+  c->cg = (float)(-gamma);
 }
-void launch_lbfgs_accept(LbfgsCtl *c, double *rho, int m, double eps, cudaStream_t s) {
-  lbfgs_accept_kernel<<<1, 32, 0, s>>>(c, rho, m, eps);
+
+void launch_lbfgs_solve(LbfgsCtl *c, const double *partials, int m, int first, double eps,
+                        double *SY, double *YY, cudaStream_t s) {
+  lbfgs_solve_kernel<<<1, 256, 0, s>>>(c, partials, dot_blocks(m), m, first, eps, SY, YY);
+}
+
+__global__ void __launch_bounds__(256) lbfgs_combine_kernel(
+    float *__restrict__ x, float *__restrict__ S, const float *__restrict__ Y, long long stride,
+    float *__restrict__ g_prev, const float *__restrict__ g, long long n,
+    const LbfgsCtl *__restrict__ c) {
+  __shared__ float cS[kMaxHistory], cY[kMaxHistory];
+  __shared__ long long off[kMaxHistory];
+  __shared__ float cg_sh;
+  __shared__ int k_sh;
+  __shared__ long long sp_off;
+  if (threadIdx.x == 0) {
+    k_sh = c->k;
+    cg_sh = c->cg;
+    sp_off = (long long)c->spare * stride;
+  }
+  for (int i = threadIdx.x; i < kMaxHistory; i += blockDim.x) {
+    cS[i] = c->cS[i];
+    cY[i] = c->cY[i];
+    off[i] = (long long)c->slot[i] * stride;
+  }
+  __syncthreads();
+  const int k = k_sh;
+  const float cg = cg_sh;
+  float *snew = S + sp_off;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gv = g[i];
+    float d = cg * gv;
+    for (int j = 0; j < k; j++) {
+      d = fmaf(cS[j], S[off[j] + i], d);
+      d = fmaf(cY[j], Y[off[j] + i], d);
+    }
+    snew[i] = d;
+    x[i] += d;
+    g_prev[i] = gv;
+  }
+}
+
+void launch_lbfgs_combine(float *x, float *S, const float *Y, long long stride, float *g_prev,
+                          const float *g, long long n, const LbfgsCtl *c, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  const int grid = (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+  lbfgs_combine_kernel<<<grid, 256, 0, s>>>(x, S, Y, stride, g_prev, g, n, c);
 }
 
 // ---- bicubic resampling ---------------------------------------------------------------------------

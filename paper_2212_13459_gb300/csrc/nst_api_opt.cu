@@ -16,8 +16,9 @@ struct nst_lbfgs {
   long long iters = 0;
   float *S = nullptr, *Y = nullptr;  // [m+1][n] history slots (device pointers)
   float *S_host = nullptr, *Y_host = nullptr;  // host allocations when the history lives there
-  float *g_prev = nullptr, *q = nullptr;
-  double *rho = nullptr, *alpha = nullptr, *partials = nullptr;
+  float *g_prev = nullptr;
+  double *SY = nullptr, *YY = nullptr;   // [m+1][m+1] s_a . y_b and y_a . y_b by slot
+  double *partials = nullptr;
   LbfgsCtl *ctl = nullptr;
 };
 
@@ -59,22 +60,19 @@ nst_status nst_lbfgs_create_ex(nst_lbfgs **out, long long n, int m, int flags) {
   }
   ok = ok &&
             cudaMalloc(&st->g_prev, n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&st->q, n * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&st->rho, slots * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&st->alpha, (size_t)m * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&st->partials, dot_partials_count() * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&st->SY, slots * slots * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&st->YY, slots * slots * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&st->partials, lbfgs_partials_count(m) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&st->ctl, sizeof(LbfgsCtl)) == cudaSuccess;
   if (!ok) {
     nst_lbfgs_destroy(st);
     return NST_ERR_OOM;
   }
-  cudaMemset(st->rho, 0, slots * sizeof(double));
-  cudaMemset(st->alpha, 0, (size_t)m * sizeof(double));
+  cudaMemset(st->SY, 0, slots * slots * sizeof(double));
+  cudaMemset(st->YY, 0, slots * slots * sizeof(double));
   LbfgsCtl c;
   std::memset(&c, 0, sizeof(c));
   c.gamma = 1.0;
-  c.one = 1.0;
-  c.t_first = 1.0;
   c.count = 0;
   c.spare = 0;
   for (int i = 0; i < kMaxHistory; i++) c.order[i] = -1;
@@ -97,8 +95,8 @@ nst_status nst_lbfgs_destroy(nst_lbfgs *st) {
     cudaFree(st->S);
     cudaFree(st->Y);
   }
-  cudaFree(st->g_prev); cudaFree(st->q);
-  cudaFree(st->rho); cudaFree(st->alpha); cudaFree(st->partials); cudaFree(st->ctl);
+  cudaFree(st->g_prev);
+  cudaFree(st->SY); cudaFree(st->YY); cudaFree(st->partials); cudaFree(st->ctl);
   delete st;
   return NST_OK;
 }
@@ -106,42 +104,15 @@ nst_status nst_lbfgs_destroy(nst_lbfgs *st) {
 nst_status nst_lbfgs_step(nst_lbfgs *st, float *x, const float *g, void *stream) {
   if (!st || !x || !g) return NST_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const long long n = st->n;
-  const int m = st->m;
-  LbfgsCtl *c = st->ctl;
-  const long long ss = st->stride;
-  const VecRef spareS{st->S, &c->spare, ss}, spareY{st->Y, &c->spare, ss};
-  if (st->iters > 0) {
-    // candidate pair: s (stored last step) and y = g - g_prev, both in the spare slot
-    launch_sub_ref(spareY, g, st->g_prev, n, s);
-    launch_dot_ref(spareY, spareS, n, st->partials, &c->ys, nullptr, nullptr, 0, s);
-    launch_dot_ref(spareY, spareY, n, st->partials, &c->yy, nullptr, nullptr, 0, s);
-    launch_lbfgs_accept(c, st->rho, m, kCurvEps, s);
-  } else {
-    launch_dot_ref(VecRef{g, nullptr, 0}, VecRef{nullptr, nullptr, 0}, n, st->partials,
-                   &c->t_first, nullptr, nullptr, 1, s);
-  }
-  // two-loop recursion: q = g; newest -> oldest: alpha_i = rho_i s_i^T q, q -= alpha_i y_i
-  if (cudaMemcpyAsync(st->q, g, n * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return NST_ERR_CUDA;
-  for (int i = 0; i < m; i++) {
-    const VecRef Si{st->S, &c->order[i], ss}, Yi{st->Y, &c->order[i], ss};
-    launch_dot_ref(Si, VecRef{st->q, nullptr, 0}, n, st->partials, &st->alpha[i], st->rho,
-                   &c->order[i], 0, s);
-    launch_axpy_ref(st->q, Yi, n, &st->alpha[i], nullptr, -1.f, s);
-  }
-  // r = gamma q; oldest -> newest: beta = rho_i y_i^T r, r += (alpha_i - beta) s_i
-  launch_scale_dev(st->q, st->q, n, &c->gamma, s);
-  for (int i = m - 1; i >= 0; i--) {
-    const VecRef Si{st->S, &c->order[i], ss}, Yi{st->Y, &c->order[i], ss};
-    double *beta = &c->beta;
-    launch_dot_ref(Yi, VecRef{st->q, nullptr, 0}, n, st->partials, beta, st->rho, &c->order[i],
-                   0, s);
-    launch_axpy_ref(st->q, Si, n, &st->alpha[i], beta, 1.f, s);
-  }
-  // d = -r; x += t d; the step goes to the spare slot for the next pair
-  launch_lbfgs_finish_ref(x, spareS, st->g_prev, st->q, g, n,
-                          st->iters == 0 ? &c->t_first : &c->one, s);
+  const int first = st->iters == 0 ? 1 : 0;
+  // 1. one pass over g, g_prev and every stored vector: y = g - g_prev into the spare slot and
+  //    all dot products of the compact representation (first call: ||g||_1)
+  launch_lbfgs_dots(g, st->g_prev, st->S, st->Y, st->stride, st->n, st->ctl, st->m, first,
+                    st->partials, s);
+  // 2. curvature test, history update, S^T Y / Y^T Y update, small solve (one CTA)
+  launch_lbfgs_solve(st->ctl, st->partials, st->m, first, kCurvEps, st->SY, st->YY, s);
+  // 3. one pass forming s = t d (into the spare slot), x += s, g_prev = g
+  launch_lbfgs_combine(x, st->S, st->Y, st->stride, st->g_prev, g, st->n, st->ctl, s);
   if (cudaGetLastError() != cudaSuccess) return NST_ERR_CUDA;
   st->iters++;
   return NST_OK;

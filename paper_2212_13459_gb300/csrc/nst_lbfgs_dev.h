@@ -5,36 +5,33 @@
 namespace nst {
 
 constexpr int kMaxHistory = 128;   // the paper uses 100 at the first scale and 10 afterwards
-
-// a vector given either directly (slot == null) or as slot *slot of a [slots][stride] array,
-// resolved on the device; an empty slot (-1) makes the consuming kernel a no-op
-struct VecRef {
-  const float *base;
-  const int *slot;
-  long long stride;
-};
+constexpr int kLbGroup = 4;        // history slots per group of the fused dot-product pass
 
 struct LbfgsCtl {
-  double ys, yy;     // y^T s and y^T y of the candidate pair
-  double gamma;      // H0 = gamma I
-  double t_first;    // min(1, 1/||g||_1) (first iteration)
-  double beta;       // scratch of the second loop
-  double one;        // 1.0 (step length of later iterations)
-  int count;         // stored pairs
-  int spare;         // slot holding the last step s (candidate pair)
-  int order[kMaxHistory];  // slots of stored pairs, newest first; -1 = empty
+  double gamma;              // H0 = gamma I: s^T y / y^T y of the newest stored pair (1 before)
+  int count;                 // stored pairs
+  int spare;                 // slot holding the last step s (the candidate pair)
+  int order[kMaxHistory];    // slots of stored pairs, newest first; -1 = empty
+  // written by the solve step for the combine step:
+  // d = cg g + sum_i (cS[i] S[slot[i]] + cY[i] Y[slot[i]]), already multiplied by the step length
+  int k;
+  int slot[kMaxHistory];
+  float cg;
+  float cS[kMaxHistory], cY[kMaxHistory];
 };
 
-void launch_dot_ref(const VecRef &a, const VecRef &b, long long n, double *partials, double *out,
-                    const double *mul_base, const int *mul_slot, int abs_mode, cudaStream_t s);
-void launch_axpy_ref(float *y, const VecRef &x, long long n, const double *c1, const double *c2,
-                     float sign, cudaStream_t s);
-void launch_sub_ref(const VecRef &out, const float *a, const float *b, long long n,
-                    cudaStream_t s);
-void launch_scale_dev(float *y, const float *x, long long n, const double *gamma, cudaStream_t s);
-void launch_lbfgs_finish_ref(float *x, const VecRef &s_next, float *g_prev, const float *r,
-                             const float *g, long long n, const double *t, cudaStream_t s);
-void launch_lbfgs_accept(LbfgsCtl *c, double *rho, int m, double eps, cudaStream_t s);
-int dot_partials_count();
+// the fused pass over the vectors: y = g - g_prev into the spare slot and, per stored pair and
+// the candidate, the four dot products s.g, y.g, s.y_new, y.y_new (first: only ||g||_1)
+void launch_lbfgs_dots(const float *g, const float *g_prev, const float *S, float *Y,
+                       long long stride, long long n, const LbfgsCtl *c, int m, int first,
+                       double *partials, cudaStream_t s);
+// one CTA: fixed-order reductions, curvature test and history bookkeeping, the compact-form
+// solve, coefficients of the step
+void launch_lbfgs_solve(LbfgsCtl *c, const double *partials, int m, int first, double eps,
+                        double *SY, double *YY, cudaStream_t s);
+// the step: s = t d into the spare slot, x += s, g_prev = g
+void launch_lbfgs_combine(float *x, float *S, const float *Y, long long stride, float *g_prev,
+                          const float *g, long long n, const LbfgsCtl *c, cudaStream_t s);
+int lbfgs_partials_count(int m);
 
 }  // namespace nst

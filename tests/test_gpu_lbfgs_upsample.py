@@ -33,6 +33,52 @@ def test_lbfgs_iterates_match_oracle(n, m, steps):
     assert iters == steps and pairs == min(m, len(opt.S))
 
 
+def test_lbfgs_long_history_follows_oracle():
+    """History 100 (the paper's first scale) filled and rolling: both sides receive the same
+    gradient sequence (the oracle's trajectory on an ill-conditioned quadratic), which keeps
+    FP32 storage from compounding through x -> g (simulated: 8e-5 after 110 steps)."""
+    n, m, steps = 3001, 100, 110
+    rng = np.random.default_rng(n)
+    d = np.logspace(-3, 1, n)
+    rng.shuffle(d)
+    b = rng.standard_normal(n)
+    x_ref = np.zeros(n)
+    opt = lbfgs.LBFGS(n, m)
+    x_gpu = torch.zeros(n, dtype=torch.float32, device="cuda")
+    st = native.LBFGS(n, m)
+    for _ in range(steps):
+        g = d * x_ref - b
+        opt.step(x_ref, g)
+        st.step(x_gpu, torch.from_numpy(g.astype(np.float32)).cuda())
+    assert len(opt.S) == m
+    pairs, _ = st.info()
+    assert pairs == m
+    xg = x_gpu.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - x_ref) <= 1e-3 * np.linalg.norm(x_ref)
+
+
+def test_lbfgs_skips_pairs_without_curvature():
+    """An indefinite quadratic: from the third pair on y^T s < 0 (well away from 0 relative to
+    |s| |y|), so the pairs are skipped and the history stays at two pairs on both sides."""
+    n, m, steps = 2000, 5, 8
+    rng = np.random.default_rng(11)
+    d = rng.uniform(-0.6, 2.0, size=n)
+    b = rng.standard_normal(n)
+    x_ref = np.zeros(n)
+    opt = lbfgs.LBFGS(n, m)
+    x_gpu = torch.zeros(n, dtype=torch.float32, device="cuda")
+    st = native.LBFGS(n, m)
+    for _ in range(steps):
+        opt.step(x_ref, d * x_ref - b)
+        xg = x_gpu.cpu().numpy().astype(np.float64)
+        st.step(x_gpu, torch.from_numpy((d * xg - b).astype(np.float32)).cuda())
+    assert len(opt.S) == 2
+    pairs, _ = st.info()
+    assert pairs == 2
+    xg = x_gpu.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(xg - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
+
+
 def test_lbfgs_first_step():
     g = torch.tensor([3.0, -1.0, 0.5, 0.0], device="cuda")
     x = torch.zeros(4, device="cuda")

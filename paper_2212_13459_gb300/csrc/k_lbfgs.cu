@@ -28,14 +28,40 @@ int lbfgs_partials_count(int m) { return 4 * (m + 1) * dot_blocks(m); }
 
 // Position p of the fused pass: p = 0 is the candidate pair (spare slot: last step s and the new
 // y), p = 1 .. count the stored pairs order[p - 1]. partials[(4 p + q) * nb + cta] for the dots
-// q = 0: s.g, 1: y.g, 2: s.y_new, 3: y.y_new.
+// q = 0: s.g, 1: y.g, 2: s.y_new, 3: y.y_new. Elements go four at a time (float4) when every
+// vector is 16-byte aligned, with all of an element group's loads issued before its FMAs.
+template <int G>
+struct DotAcc {
+  double acc[G][4];
+  float part[G][4];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int j = 0; j < G; j++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[j][q] = 0.0, part[j][q] = 0.f;
+  }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int j = 0; j < G; j++)
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[j][q] += (double)part[j][q], part[j][q] = 0.f;
+  }
+  __device__ __forceinline__ void add(int j, float sv, float wv, float gv, float yv) {
+    part[j][0] = fmaf(sv, gv, part[j][0]);
+    part[j][1] = fmaf(wv, gv, part[j][1]);
+    part[j][2] = fmaf(sv, yv, part[j][2]);
+    part[j][3] = fmaf(wv, yv, part[j][3]);
+  }
+};
+
 __global__ void __launch_bounds__(kDotThreads) lbfgs_dots_kernel(
     const float *__restrict__ g, const float *__restrict__ g_prev, const float *__restrict__ S,
     float *__restrict__ Y, long long stride, long long n, const LbfgsCtl *__restrict__ c,
-    int first, double *__restrict__ partials) {
+    int first, int vec, double *__restrict__ partials) {
   constexpr int G = kLbGroup;
-  __shared__ int sl[G];
-  __shared__ int nj_sh, sp_sh;
+  __shared__ long long off[G];
+  __shared__ int nj_sh;
+  __shared__ long long sp_off;
   __shared__ double red[kDotThreads / 32][4 * G];
   const int grp = blockIdx.y, nb = gridDim.x;
   if (threadIdx.x == 0) {
@@ -43,65 +69,75 @@ __global__ void __launch_bounds__(kDotThreads) lbfgs_dots_kernel(
     int nj = 0;
     for (int j = 0; j < G; j++) {
       const int p = grp * G + j;
+      off[j] = 0;
       if (p <= count) {
-        sl[j] = p == 0 ? c->spare : c->order[p - 1];
+        off[j] = (long long)(p == 0 ? c->spare : c->order[p - 1]) * stride;
         nj = j + 1;
       }
     }
     nj_sh = first ? (grp == 0 ? 1 : 0) : nj;
-    sp_sh = c->spare;
+    sp_off = (long long)c->spare * stride;
   }
   __syncthreads();
   const int nj = nj_sh;
   if (nj == 0) return;
-  float *ynew = first ? nullptr : Y + (size_t)sp_sh * stride;
-  const long long step = (long long)nb * kDotThreads;
-  double acc[G][4];
-  float part[G][4];
-#pragma unroll
-  for (int j = 0; j < G; j++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) acc[j][q] = 0.0, part[j][q] = 0.f;
+  float *ynew = Y + sp_off;
+  const bool own_y = grp == 0;   // group 0 holds the candidate (position 0) and writes its y
+  const long long tstride = (long long)nb * kDotThreads;
+  const long long t0 = (long long)blockIdx.x * kDotThreads + threadIdx.x;
+  DotAcc<G> A;
+  A.clear();
   int chunk = 0;
-  for (long long i = (long long)blockIdx.x * kDotThreads + threadIdx.x; i < n; i += step) {
-    const float gv = g[i];
+  const long long n4 = vec ? n / 4 : 0;
+  for (long long v = t0; v < n4; v += tstride) {
+    const float4 gv = reinterpret_cast<const float4 *>(g)[v];
     if (first) {
-      part[0][0] += fabsf(gv);
+      A.part[0][0] += fabsf(gv.x) + fabsf(gv.y) + fabsf(gv.z) + fabsf(gv.w);
     } else {
-      const float yv = gv - g_prev[i];
-      if (grp == 0) ynew[i] = yv;
+      const float4 gp = reinterpret_cast<const float4 *>(g_prev)[v];
+      const float4 yv = make_float4(gv.x - gp.x, gv.y - gp.y, gv.z - gp.z, gv.w - gp.w);
+      if (own_y) reinterpret_cast<float4 *>(ynew)[v] = yv;
+      float4 sv[G], wv[G];
 #pragma unroll
       for (int j = 0; j < G; j++) {
         if (j < nj) {
-          const size_t o = (size_t)sl[j] * stride + i;
-          const float sv = S[o];
-          const float wv = (grp == 0 && j == 0) ? yv : Y[o];
-          part[j][0] = fmaf(sv, gv, part[j][0]);
-          part[j][1] = fmaf(wv, gv, part[j][1]);
-          part[j][2] = fmaf(sv, yv, part[j][2]);
-          part[j][3] = fmaf(wv, yv, part[j][3]);
+          sv[j] = reinterpret_cast<const float4 *>(S + off[j])[v];
+          wv[j] = (own_y && j == 0) ? yv : reinterpret_cast<const float4 *>(Y + off[j])[v];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < G; j++) {
+        if (j < nj) {
+          A.add(j, sv[j].x, wv[j].x, gv.x, yv.x);
+          A.add(j, sv[j].y, wv[j].y, gv.y, yv.y);
+          A.add(j, sv[j].z, wv[j].z, gv.z, yv.z);
+          A.add(j, sv[j].w, wv[j].w, gv.w, yv.w);
         }
       }
     }
-    if (++chunk == 16) {   // FP32 over 16 elements, FP64 across chunks
-      chunk = 0;
+    if (++chunk == 4) { chunk = 0; A.flush(); }   // FP32 over 16 elements, FP64 across chunks
+  }
+  for (long long i = n4 * 4 + t0; i < n; i += tstride) {   // scalar path / tail
+    const float gv = g[i];
+    if (first) {
+      A.part[0][0] += fabsf(gv);
+    } else {
+      const float yv = gv - g_prev[i];
+      if (own_y) ynew[i] = yv;
 #pragma unroll
       for (int j = 0; j < G; j++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[j][q] += (double)part[j][q], part[j][q] = 0.f;
+        if (j < nj) A.add(j, S[off[j] + i], (own_y && j == 0) ? yv : Y[off[j] + i], gv, yv);
     }
+    if (++chunk == 16) { chunk = 0; A.flush(); }
   }
-#pragma unroll
-  for (int j = 0; j < G; j++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) acc[j][q] += (double)part[j][q];
+  A.flush();
   // fixed-order block reduction: warp shuffles, then the warps in index order
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < G; j++)
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      double v = acc[j][q];
+      double v = A.acc[j][q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) red[warp][j * 4 + q] = v;
@@ -115,11 +151,16 @@ __global__ void __launch_bounds__(kDotThreads) lbfgs_dots_kernel(
   }
 }
 
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 void launch_lbfgs_dots(const float *g, const float *g_prev, const float *S, float *Y,
                        long long stride, long long n, const LbfgsCtl *c, int m, int first,
                        double *partials, cudaStream_t s) {
   dim3 grid(dot_blocks(m), first ? 1 : dot_groups(m));
-  lbfgs_dots_kernel<<<grid, kDotThreads, 0, s>>>(g, g_prev, S, Y, stride, n, c, first, partials);
+  const int vec = aligned16(g) && aligned16(g_prev) && aligned16(S) && aligned16(Y) &&
+                  stride % 4 == 0;
+  lbfgs_dots_kernel<<<grid, kDotThreads, 0, s>>>(g, g_prev, S, Y, stride, n, c, first, vec,
+                                                 partials);
 }
 
 __global__ void __launch_bounds__(256) lbfgs_solve_kernel(LbfgsCtl *__restrict__ c,
@@ -216,7 +257,8 @@ void launch_lbfgs_solve(LbfgsCtl *c, const double *partials, int m, int first, d
 __global__ void __launch_bounds__(256) lbfgs_combine_kernel(
     float *__restrict__ x, float *__restrict__ S, const float *__restrict__ Y, long long stride,
     float *__restrict__ g_prev, const float *__restrict__ g, long long n,
-    const LbfgsCtl *__restrict__ c) {
+    const LbfgsCtl *__restrict__ c, int vec) {
+  constexpr int U = 8;   // stored pairs whose loads are issued together
   __shared__ float cS[kMaxHistory], cY[kMaxHistory];
   __shared__ long long off[kMaxHistory];
   __shared__ float cg_sh;
@@ -236,14 +278,42 @@ __global__ void __launch_bounds__(256) lbfgs_combine_kernel(
   const int k = k_sh;
   const float cg = cg_sh;
   float *snew = S + sp_off;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long tstride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n4 = vec ? n / 4 : 0;
+  for (long long v = t0; v < n4; v += tstride) {
+    const float4 gv = reinterpret_cast<const float4 *>(g)[v];
+    float4 d = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
+    for (int j0 = 0; j0 < k; j0 += U) {
+      float4 sv[U], yv[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (j0 + u < k) {
+          sv[u] = reinterpret_cast<const float4 *>(S + off[j0 + u])[v];
+          yv[u] = reinterpret_cast<const float4 *>(Y + off[j0 + u])[v];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (j0 + u < k) {
+          const float a = cS[j0 + u], b = cY[j0 + u];
+          d.x = fmaf(b, yv[u].x, fmaf(a, sv[u].x, d.x));
+          d.y = fmaf(b, yv[u].y, fmaf(a, sv[u].y, d.y));
+          d.z = fmaf(b, yv[u].z, fmaf(a, sv[u].z, d.z));
+          d.w = fmaf(b, yv[u].w, fmaf(a, sv[u].w, d.w));
+        }
+      }
+    }
+    reinterpret_cast<float4 *>(snew)[v] = d;
+    float4 xv = reinterpret_cast<float4 *>(x)[v];
+    xv.x += d.x; xv.y += d.y; xv.z += d.z; xv.w += d.w;
+    reinterpret_cast<float4 *>(x)[v] = xv;
+    reinterpret_cast<float4 *>(g_prev)[v] = gv;
+  }
+  for (long long i = n4 * 4 + t0; i < n; i += tstride) {   // scalar path / tail
     const float gv = g[i];
     float d = cg * gv;
-    for (int j = 0; j < k; j++) {
-      d = fmaf(cS[j], S[off[j] + i], d);
-      d = fmaf(cY[j], Y[off[j] + i], d);
-    }
+    for (int j = 0; j < k; j++) d = fmaf(cY[j], Y[off[j] + i], fmaf(cS[j], S[off[j] + i], d));
     snew[i] = d;
     x[i] += d;
     g_prev[i] = gv;
@@ -252,9 +322,11 @@ __global__ void __launch_bounds__(256) lbfgs_combine_kernel(
 
 void launch_lbfgs_combine(float *x, float *S, const float *Y, long long stride, float *g_prev,
                           const float *g, long long n, const LbfgsCtl *c, cudaStream_t s) {
-  long long b = (n + 255) / 256;
+  const int vec = aligned16(x) && aligned16(S) && aligned16(Y) && aligned16(g_prev) &&
+                  aligned16(g) && stride % 4 == 0;
+  long long b = (n / 4 + 255) / 256;
   const int grid = (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
-  lbfgs_combine_kernel<<<grid, 256, 0, s>>>(x, S, Y, stride, g_prev, g, n, c);
+  lbfgs_combine_kernel<<<grid, 256, 0, s>>>(x, S, Y, stride, g_prev, g, n, c, vec);
 }
 
 // ---- bicubic resampling ---------------------------------------------------------------------------

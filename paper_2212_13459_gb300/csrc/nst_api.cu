@@ -467,7 +467,7 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
   const BlockGeom *geom = p.d_geom + bt.t0;
   {
     Timer tm(ctx, kTOther, s);
-    ctx->launches++;
+    ctx->launches += ctx->use_tc ? 2 : 1;   // tensor-core form: staging + convolution
     if (ctx->use_tc) {
       // the staged BF16-pair image goes to the (not yet used) second gradient buffer
       cudaError_t e = launch_conv11_fwd_tc(img, p.H, p.W, ctx->d_w11, ctx->d_bias[0], geom, bt.B,
@@ -720,7 +720,7 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   fa.r_is_bf16 = ctx->bf16 ? 1 : 0;
   fa.beta = ctx->d_fin;
   fa.partial = ctx->d_fin + kNStyle * 512;
-  ctx->launches++;
+  ctx->launches += 3;   // moments, residuals, sums
   launch_style_finalize(fa, s);
   // Step 2: loss and gradient block by block
   CK(cudaMemsetAsync(ctx->d_parts + kNStyle, 0, sizeof(double), s));

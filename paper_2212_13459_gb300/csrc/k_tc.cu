@@ -81,63 +81,43 @@ __device__ __forceinline__ void unpool_store32(const ConvArgs &a, const BlockGeo
                                                int x, int n, const float *v) {
   const int Hf = a.Hb * 2, Wf = a.Wb * 2, C = a.cout;
   const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
-  const uint4 *act = reinterpret_cast<const uint4 *>(a.unpool_act);
-  uint4 *out = reinterpret_cast<uint4 *>(a.unpool_out);
-  size_t o[4];   // in 16-byte units
-  o[0] = ((((size_t)b * Hf + 2 * y) * Wf + 2 * x) * C + n) / 8;
-  o[1] = o[0] + C / 8;
-  o[2] = o[0] + (size_t)Wf * C / 8;
-  o[3] = o[2] + C / 8;
-  // every load of the four windows first (16 x 16 bytes in flight per thread), then the routing
-  uint4 w[4][4];
-#pragma unroll
-  for (int k = 0; k < 4; k++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) w[k][q] = valid ? act[o[k] + q] : make_uint4(0u, 0u, 0u, 0u);
+  const __nv_bfloat16 *act = reinterpret_cast<const __nv_bfloat16 *>(a.unpool_act);
+  __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.unpool_out);
+  size_t o[4];
+  o[0] = (((size_t)b * Hf + 2 * y) * Wf + 2 * x) * C + n;
+  o[1] = o[0] + C;
+  o[2] = o[0] + (size_t)Wf * C;
+  o[3] = o[2] + C;
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     float r[4][8];
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-#pragma unroll
-      for (int j = 0; j < 8; j++) r[k][j] = 0.f;
     if (valid) {
-      float wf[4][8];
+      float w[4][8];
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&w[k][q]);
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const float2 f = __bfloat1622float2(h[i]);
-          wf[k][2 * i] = f.x;
-          wf[k][2 * i + 1] = f.y;
-        }
-      }
+      for (int k = 0; k < 4; k++) ld_bf16x8(act + o[k] + 8 * q, w[k]);
 #pragma unroll
       for (int j = 0; j < 8; j++) {
         int km = 0;
-        float am = wf[0][j];
+        float am = w[0][j];
 #pragma unroll
         for (int k = 1; k < 4; k++)
-          if (wf[k][j] > am) { am = wf[k][j]; km = k; }
+          if (w[k][j] > am) { am = w[k][j]; km = k; }
         const float gv = __bfloat162float(__float2bfloat16_rn(v[8 * q + j]));
         const float val = am > 0.f ? gv : 0.f;
 #pragma unroll
         for (int k = 0; k < 4; k++) r[k][j] = k == km ? val : 0.f;
       }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) r[k][j] = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      uint4 t;
-      __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&t);
-#pragma unroll
-      for (int i = 0; i < 4; i++) h[i] = __floats2bfloat162_rn(r[k][2 * i], r[k][2 * i + 1]);
-      out[o[k] + q] = t;
-    }
+    for (int k = 0; k < 4; k++) st_bf16x8(out + o[k] + 8 * q, r[k]);
   }
 }
 
-template <bool UNPOOL>
 __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g, int b, int y,
                                            int x, int n, float *v) {
   const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
@@ -189,7 +169,7 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
       }
     }
   }
-  if constexpr (UNPOOL) {
+  if (a.unpool_out) {
     unpool_store32(a, g, b, y, x, n, v);
     return;
   }
@@ -235,7 +215,7 @@ __device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGe
 }
 
 // ---- the kernel -------------------------------------------------------------------------------------
-template <int BN, int STAGES, bool UNPOOL>
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2,
@@ -362,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
-        if (inb) epilogue32<UNPOOL>(a, g, b, y, x, nt * BN + c, v);
+        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
         if (a.pool_out) {
           if (!inb) {
 #pragma unroll
@@ -406,7 +386,7 @@ struct HaloCfg {
   static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloStage;
 };
 
-template <int BN, int KB, int P2KB, int NT, bool UNPOOL>
+template <int BN, int KB, int P2KB, int NT>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
@@ -560,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
-        if (inb) epilogue32<UNPOOL>(a, g, b, y, x, nt * BN + c, v);
+        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
         if (a.pool_out) {
           if (!inb) {
 #pragma unroll
@@ -596,7 +576,7 @@ constexpr uint32_t kSwapA = kSwapBN * kBK * 2;  // 16 KB weight box
 constexpr uint32_t kSwapB = kSwapBP * kBK * 2;  // 32 KB activation box
 constexpr uint32_t kSwapT = 32 * 32 * 4;        // transpose tile per epilogue warp
 
-template <int STAGES, bool UNPOOL>
+template <int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_swap_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
@@ -742,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int pp = c + lane;   // this lane's pixel of the patch, channels n .. n+31 in v
         const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
         const bool inb = pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb;
-        if (inb) epilogue32<UNPOOL>(a, g, b, y, x, n, v);
+        if (inb) epilogue32(a, g, b, y, x, n, v);
         if (a.pool_out) {
           if (!inb) {
 #pragma unroll
@@ -818,24 +798,24 @@ cudaError_t encode_wt(CUtensorMap *m, const void *ptr, int N, int K, int BN) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, int STAGES, bool UNPOOL = false>
+template <int BN, int STAGES>
 cudaError_t launch_bn(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                       const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
                       cudaStream_t s) {
   constexpr size_t smem = (size_t)STAGES * (128 * kBK * 2 + BN * kBK * 2) + 1024;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, UNPOOL>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int grid = std::min(tg.total, g_num_sms);
-  conv_tc_kernel<BN, STAGES, UNPOOL><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
+  conv_tc_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
   return cudaGetLastError();
 }
 
-template <int STAGES, bool UNPOOL>
+template <int STAGES>
 cudaError_t launch_swap(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
                         cudaStream_t s) {
@@ -843,13 +823,13 @@ cudaError_t launch_swap(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   static_assert(smem <= 227 * 1024, "pixels-as-N kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_swap_kernel<STAGES, UNPOOL>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_swap_kernel<STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int grid = std::min(tg.total, g_num_sms);
-  conv_tc_swap_kernel<STAGES, UNPOOL><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
+  conv_tc_swap_kernel<STAGES><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a, tg);
   return cudaGetLastError();
 }
 
@@ -874,7 +854,7 @@ void pick_patch_rows(int H, int W, int rows, int &TH, int &TW, bool pool) {
   }
 }
 
-template <int BN, int KB, int P2KB, int NT, bool UNPOOL = false>
+template <int BN, int KB, int P2KB, int NT>
 cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, cudaStream_t s) {
   using Cfg = HaloCfg<BN, KB, P2KB, NT>;
@@ -882,7 +862,7 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   static_assert(Cfg::SMEM <= kHaloSmemMax, "halo kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2KB, NT, UNPOOL>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2KB, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
@@ -897,8 +877,7 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   tg.total = a.B * tg.tiles_x * tg.tiles_y;   // M tiles; every slice covers all of them
   int grid = std::min(tg.total * NT, g_num_sms);
   grid = std::max(NT, grid / NT * NT);
-  conv_tc_halo_kernel<BN, KB, P2KB, NT, UNPOOL><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2, a,
-                                                                                 tg);
+  conv_tc_halo_kernel<BN, KB, P2KB, NT><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2, a, tg);
   return cudaGetLastError();
 }
 
@@ -940,11 +919,6 @@ cudaError_t launch_conv_tc_halo(const ConvArgs &a, int BN, int KB, int P2KB, int
   } else {
     mA2 = mA;
     mB2 = mB;
-  }
-  if (a.unpool_out) {   // only the input gradient of conv2_1 routes through a pool here
-    if (BN == 64 && KB == 2 && P2KB == 0 && NT == 1)
-      return launch_halo<64, 2, 0, 1, true>(mA, mB, mA2, mB2, a, s);
-    return cudaErrorInvalidValue;
   }
   if (BN == 64 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<64, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
   if (BN == 64 && KB == 1 && P2KB == 1 && NT == 1) return launch_halo<64, 1, 1, 1>(mA, mB, mA2, mB2, a, s);
@@ -998,11 +972,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   }
   if (!a.taps) { mA = mA2; mB = mB2; }
   if (!a.k2) { mA2 = mA; mB2 = mB; }
-  if (swap)
-    return a.unpool_out ? launch_swap<4, true>(mA, mB, mA2, mB2, a, tg, s)
-                        : launch_swap<4, false>(mA, mB, mA2, mB2, a, tg, s);
-  if (a.unpool_out)
-    return BN == 256 ? launch_bn<256, 4, true>(mA, mB, mA2, mB2, a, tg, s) : cudaErrorInvalidValue;
+  if (swap) return launch_swap<4>(mA, mB, mA2, mB2, a, tg, s);
   switch (BN) {
     case 64: return launch_bn<64, 8>(mA, mB, mA2, mB2, a, tg, s);
     case 128: return launch_bn<128, 6>(mA, mB, mA2, mB2, a, tg, s);

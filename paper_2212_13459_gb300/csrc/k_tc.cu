@@ -72,52 +72,6 @@ __device__ __forceinline__ void st_bf16x8(__nv_bfloat16 *p, const float *v) {
   *reinterpret_cast<uint4 *>(p) = t;
 }
 
-// Max-unpool fused into the input-gradient epilogue (Alg. 1 backward through a pooling layer):
-// the gradient at pooled pixel (y, x) (rounded to BF16, as the unfused path stores it) goes to
-// the first maximum of its 2 x 2 window of the pool's input activation (row-major window order,
-// strict '>'), gated by that activation being > 0; the other three pixels get 0, and so do all
-// four children of a pooled pixel outside the block's valid region.
-__device__ __forceinline__ void unpool_store32(const ConvArgs &a, const BlockGeom &g, int b, int y,
-                                               int x, int n, const float *v) {
-  const int Hf = a.Hb * 2, Wf = a.Wb * 2, C = a.cout;
-  const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
-  const __nv_bfloat16 *act = reinterpret_cast<const __nv_bfloat16 *>(a.unpool_act);
-  __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.unpool_out);
-  size_t o[4];
-  o[0] = (((size_t)b * Hf + 2 * y) * Wf + 2 * x) * C + n;
-  o[1] = o[0] + C;
-  o[2] = o[0] + (size_t)Wf * C;
-  o[3] = o[2] + C;
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    float r[4][8];
-    if (valid) {
-      float w[4][8];
-#pragma unroll
-      for (int k = 0; k < 4; k++) ld_bf16x8(act + o[k] + 8 * q, w[k]);
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        int km = 0;
-        float am = w[0][j];
-#pragma unroll
-        for (int k = 1; k < 4; k++)
-          if (w[k][j] > am) { am = w[k][j]; km = k; }
-        const float gv = __bfloat162float(__float2bfloat16_rn(v[8 * q + j]));
-        const float val = am > 0.f ? gv : 0.f;
-#pragma unroll
-        for (int k = 0; k < 4; k++) r[k][j] = k == km ? val : 0.f;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; k++)
-#pragma unroll
-        for (int j = 0; j < 8; j++) r[k][j] = 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++) st_bf16x8(out + o[k] + 8 * q, r[k]);
-  }
-}
-
 __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g, int b, int y,
                                            int x, int n, float *v) {
   const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
@@ -168,10 +122,6 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
         }
       }
     }
-  }
-  if (a.unpool_out) {
-    unpool_store32(a, g, b, y, x, n, v);
-    return;
   }
   __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out) + o;
 #pragma unroll

@@ -627,15 +627,9 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
         a.two_lambda = 2.f * ctx->cfg.lambda_c;
       }
     }
-    // tensor-core engine: the max-unpool runs in the convolution's epilogue
-    const bool fuse_unpool = kPoolAfter[lp] && ctx->use_tc;
-    if (fuse_unpool) {
-      a.unpool_act = ws.act[lp];
-      a.unpool_out = ws.g[1 - cur];
-    }
     nst_status st = run_conv(ctx, a, s);
     if (st) return st;
-    if (kPoolAfter[lp] && !fuse_unpool) {
+    if (kPoolAfter[lp]) {
       Timer tm(ctx, kTOther, s);
       ctx->launches++;
       launch_unpool<T>((const T *)ws.g[1 - cur], (const T *)ws.act[lp], (T *)ws.g[cur], bt.B,

@@ -78,11 +78,6 @@ struct ConvArgs {
                           // [B][Hb/2][Wb/2][cout] (null = no fused pooling)
   const float *addvec;    // backward: per-channel term added at valid pixels before the gate
                           // (alpha of the mean / std loss, Table 1 rows 3-4), or null
-  // backward, tensor-core engine: this gradient is w.r.t. the output of a 2x2 max pool; route it
-  // through the pool and the ReLU before it (act: the pool's input [B][2Hb][2Wb][cout], the
-  // post-ReLU activation) and write the result to unpool_out [B][2Hb][2Wb][cout] instead of out
-  const void *unpool_act;
-  void *unpool_out;
 };
 
 }  // namespace nst

@@ -125,26 +125,19 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
   }
 }
 
-// Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials. One warp per
-// element: lane l sums runs l, l + 32, ... in order, then a fixed shuffle tree adds the lanes,
-// so the result does not depend on the launch shape.
-__global__ void __launch_bounds__(256) gram_tc_reduce_kernel(const float *__restrict__ part,
-                                                             int nruns, int C, int N, int nI,
-                                                             int nJ, double *__restrict__ Gacc) {
+// Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials
+__global__ void gram_tc_reduce_kernel(const float *__restrict__ part, int nruns, int C, int N,
+                                      int nI, int nJ, double *__restrict__ Gacc) {
   const long long n = (long long)C * C;
-  const int lane = threadIdx.x & 31;
-  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-  const size_t stride = (size_t)nI * nJ * 128 * N;
-  for (long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < n;
-       e += warps) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / C), j = (int)(e % C);
     const int tile = (i / 128) * nJ + j / N;
     const size_t off = ((size_t)tile * 128 + (i % 128)) * N + (j % N);
+    const size_t stride = (size_t)nI * nJ * 128 * N;
     double s = 0.0;
-    for (int r = lane; r < nruns; r += 32) s += (double)part[(size_t)r * stride + off];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) Gacc[e] += s;
+    for (int r = 0; r < nruns; r++) s += (double)part[(size_t)r * stride + off];
+    Gacc[e] += s;
   }
 }
 
@@ -212,7 +205,7 @@ cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStr
   }
   if (e != cudaSuccess) return e;
   const long long n = (long long)a.C * a.C;
-  const int grid = (int)std::min<long long>((n + 7) / 8, 152 * 16);   // 8 warps per CTA
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 8);
   gram_tc_reduce_kernel<<<grid, 256, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
   return cudaGetLastError();
 }

@@ -524,85 +524,7 @@ constexpr int kSwapBN = 128;                    // output channels per tile (M)
 constexpr int kSwapBP = 256;                    // output pixels per tile (N)
 constexpr uint32_t kSwapA = kSwapBN * kBK * 2;  // 16 KB weight box
 constexpr uint32_t kSwapB = kSwapBP * kBK * 2;  // 32 KB activation box
-
-// the eight 2 x 2 windows of a 32-pixel chunk (whole patch rows of width TW), in-thread
-template <int TW>
-__device__ __forceinline__ void swap_pool_chunk(const ConvArgs &a, const BlockGeom &g, int b,
-                                                int tx, int ty, const TcGeom &tg, int c, int py0,
-                                                int ch, const float *vals) {
-  const int Hp = a.Hb >> 1, Wp = a.Wb >> 1;
-  const int pehl = g.eh >> (a.level + 1), pewl = g.ew >> (a.level + 1);
-  const int npix = tg.TH * TW;
-  __nv_bfloat16 *pout = reinterpret_cast<__nv_bfloat16 *>(a.pool_out);
-#pragma unroll
-  for (int w = 0; w < 8; w++) {
-    constexpr int WPR = TW / 2;   // windows per patch row pair
-    const int wr = w / WPR, wc = w % WPR;
-    const int j0 = 2 * wr * TW + 2 * wc;
-    const int y = ty * tg.TH + py0 + 2 * wr, x = tx * TW + 2 * wc;
-    if (y >= a.Hb || x >= a.Wb || c + j0 >= npix) continue;
-    const float m = fmaxf(fmaxf(vals[j0], vals[j0 + 1]), fmaxf(vals[j0 + TW], vals[j0 + TW + 1]));
-    const int py = y >> 1, px = x >> 1;
-    const bool pv = py < pehl && px < pewl;
-    pout[(((size_t)b * Hp + py) * Wp + px) * a.cout + ch] = __float2bfloat16_rn(pv ? m : 0.f);
-  }
-}
-
-// Epilogue of one 32-pixel chunk in the accumulator's own layout (lane = output channel ch,
-// v[j] = pixel c + j of the patch): bias / ReLU / valid mask (forward) or addvec / ReLU gate
-// (backward) per element, 2-byte stores that a warp issues as 64 contiguous bytes per pixel,
-// and the fused 2 x 2 max pool inside the thread (a chunk holds whole window rows). Same
-// arithmetic and rounding as epilogue32 / pool_epilogue32 (no content term).
-__device__ __forceinline__ void swap_epilogue_direct(const ConvArgs &a, const BlockGeom &g, int b,
-                                                     int tx, int ty, const TcGeom &tg, int c,
-                                                     int ch, const float *v) {
-  const int npix = tg.TH * tg.TW;
-  const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
-  const size_t rowstride = (size_t)a.Wb * a.cout;
-  const size_t base = (size_t)b * a.Hb * rowstride + ch;
-  __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out);
-  const int py0 = c / tg.TW, px0 = c - py0 * tg.TW;
-  // pixel j of the chunk: patch position advanced incrementally (no per-pixel arrays kept)
-  auto walk = [&](auto &&body) {
-    int py = py0, px = px0;
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-      const int y = ty * tg.TH + py, x = tx * tg.TW + px;
-      const bool in = c + j < npix && y < a.Hb && x < a.Wb;
-      body(j, in, in && y < ehl && x < ewl, base + (size_t)(y * a.Wb + x) * a.cout);
-      if (++px == tg.TW) { px = 0; ++py; }
-    }
-  };
-  if (a.mode == kEpiForward) {
-    const float bias = __ldg(a.bias + ch);
-    float vals[32];
-    walk([&](int j, bool in, bool valid, size_t o) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(valid ? fmaxf(v[j] + bias, 0.f) : 0.f);
-      vals[j] = __bfloat162float(h);
-      if (in) out[o] = h;
-    });
-    if (a.pool_out) {   // TW is 8 or 16 and the chunk starts on an even patch row
-      if (tg.TW == 16)
-        swap_pool_chunk<16>(a, g, b, tx, ty, tg, c, py0, ch, vals);
-      else
-        swap_pool_chunk<8>(a, g, b, tx, ty, tg, c, py0, ch, vals);
-    }
-  } else {
-    const float add = a.addvec ? __ldg(a.addvec + ch) : 0.f;
-    float mk[32];
-    if (a.mask) {
-      const __nv_bfloat16 *mp = reinterpret_cast<const __nv_bfloat16 *>(a.mask);
-      walk([&](int j, bool, bool valid, size_t o) {
-        mk[j] = valid ? __bfloat162float(mp[o]) : 0.f;
-      });
-    }
-    walk([&](int j, bool in, bool valid, size_t o) {
-      float r = valid ? v[j] + add : 0.f;
-      if (a.mask) r = mk[j] > 0.f ? r : 0.f;
-      if (in) out[o] = __float2bfloat16_rn(r);
-    });
-  }
-}
+constexpr uint32_t kSwapT = 32 * 32 * 4;        // transpose tile per epilogue warp
 
 template <int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -714,6 +636,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;            // TMEM lane quarter = channels q*32 .. q*32+31 of the tile
     const int half = (warp - 2) >> 2;  // pixels half*128 .. half*128+127 of the patch
+    uint8_t *tsm = smem_gen + STAGES * STAGE_BYTES + (size_t)(warp - 2) * kSwapT;
     int it = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
@@ -730,7 +653,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = half * (kSwapBP / 2); c < (half + 1) * (kSwapBP / 2); c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);   // v[j] = D[channel n + lane][pixel c + j]
-        swap_epilogue_direct(a, g, b, tx, ty, tg, c, n + lane, v);
+        // transpose: row j of the tile = pixel c + j, 16-byte chunk (lane / 4) ^ (j % 8)
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+          *reinterpret_cast<float *>(tsm + j * 128 + ((((lane >> 2) ^ (j & 7)) << 4) |
+                                                      ((lane & 3) << 2))) = v[j];
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const float4 f = *reinterpret_cast<const float4 *>(tsm + lane * 128 +
+                                                             ((k ^ (lane & 7)) << 4));
+          v[4 * k] = f.x;
+          v[4 * k + 1] = f.y;
+          v[4 * k + 2] = f.z;
+          v[4 * k + 3] = f.w;
+        }
+        __syncwarp();
+        const int pp = c + lane;   // this lane's pixel of the patch, channels n .. n+31 in v
+        const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
+        const bool inb = pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb;
+        if (inb) epilogue32(a, g, b, y, x, n, v);
+        if (a.pool_out) {
+          if (!inb) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] = 0.f;
+          }
+          pool_epilogue32(a, g, b, y, x, n, tg.TW, v);
+        }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
@@ -820,7 +769,7 @@ template <int STAGES>
 cudaError_t launch_swap(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
                         cudaStream_t s) {
-  constexpr size_t smem = (size_t)STAGES * (kSwapA + kSwapB) + 1024;
+  constexpr size_t smem = (size_t)STAGES * (kSwapA + kSwapB) + 8 * kSwapT + 1024;
   static_assert(smem <= 227 * 1024, "pixels-as-N kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
@@ -949,7 +898,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   int hBN, hKB, hP2, hNT;
   if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
   // 128 output channels: pixels as the MMA's N (256 wide) instead of channels (128 wide)
-  const bool swap = a.cout == kSwapBN && !a.cact;
+  const bool swap = a.cout == kSwapBN;
   const int BN = swap ? kSwapBN : (a.cout >= 256 ? 256 : a.cout);
   TcGeom tg;
   pick_patch_rows(a.Hb, a.Wb, swap ? kSwapBP : 128, tg.TH, tg.TW, a.pool_out != nullptr);

@@ -199,7 +199,8 @@ def run_ours(args, rank, world, local_rank):
     else:
         x.copy_(torch.clamp(0.5 * u + 0.25, 0, 1))
     ctx = native.Context(flat, tiles_h=k, tiles_w=k, precision=prec,
-                         margin1=args.margin1, margin2=args.margin2)
+                         margin1=args.margin1, margin2=args.margin2,
+                         workspace_limit_bytes=int(args.workspace_gb * 1e9))
     ctx.style_targets(v)
     ctx.content_targets(u)
     grad = torch.empty_like(x)
@@ -211,6 +212,7 @@ def run_ours(args, rank, world, local_rank):
         raise RuntimeError("device status after warm-up: %s" % native.lib().nst_last_error(ctx.h))
     free_b, total_b = torch.cuda.mem_get_info(dev)
     hbm_used_gb = (total_b - free_b) / 1e9
+    step2_batches, resident = ctx.pass_info()
     # ---- timed region: K evaluations, CUDA events on the launching stream ----
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -249,7 +251,8 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
     report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E, status, e2e,
-           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist, hbm_used_gb)
+           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist, hbm_used_gb,
+           (step2_batches, resident))
 
 
 def e2e_leg(ctx, x, H, W, args, dist, dev, world):
@@ -302,7 +305,7 @@ def lbfgs_leg(x, grad, H, W, stream, dev):
 
 
 def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E, status, e2e,
-           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist, hbm_used_gb=None):
+           lbfgs_ms, t_up, flat, u, v, x, grad, dev, dist, hbm_used_gb=None, pass_info=None):
     from paper_2212_13459_gb300 import native
     peaks = load_peaks()
     conv_tflops = tm["conv_flops"] / (tm["conv_ms"] / 1e3) / 1e12 if tm["conv_ms"] > 0 else None
@@ -330,6 +333,9 @@ def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E
                    "H": H, "W": W, "blocks": "%dx%d" % (k, k), "engine": "tcgen05" if
                    prec == native.PREC_BF16 else "fp32-simt",
                    "l2": "inputs larger than L2 (activations of one pass >> 129 MB); no flush",
+                   "step2_batches": pass_info[0] if pass_info else None,
+                   "resident": pass_info[1] if pass_info else None,
+                   "workspace_limit_gb": args.workspace_gb,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pct_bf16_peak_algorithmic": 100.0 * alg_tflops / peaks["bf16_sus"],
         "algorithmic_tflops": alg_tflops,
@@ -363,7 +369,8 @@ def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev):
     import torch
     from paper_2212_13459_gb300 import native
     ctx = native.Context(flat, tiles_h=k, tiles_w=k, precision=native.PREC_FP32,
-                         margin1=args.margin1, margin2=args.margin2)
+                         margin1=args.margin1, margin2=args.margin2,
+                         workspace_limit_bytes=int(args.workspace_gb * 1e9))
     ctx.style_targets(v)
     ctx.content_targets(u)
     g32 = torch.empty_like(x)
@@ -410,6 +417,9 @@ def main():
     ap.add_argument("--workload", default="scale3", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--tiles", type=int, default=0)
+    ap.add_argument("--workspace-gb", dest="workspace_gb", type=float, default=160.0,
+                    help="block workspace limit; all blocks of Step 2 fit in one batch (one "
+                         "forward pass serves both steps) when it allows")
     ap.add_argument("--margin1", type=int, default=80)
     ap.add_argument("--margin2", type=int, default=160)
     ap.add_argument("--compare-fp32", dest="compare_fp32", action="store_true", default=True)

@@ -131,6 +131,14 @@ nst_status nst_get_timing(nst_ctx *ctx, double *out6, void *stream);
 /* Enable or disable per-launch event timing; either way the counters restart from zero. */
 nst_status nst_set_timing(nst_ctx *ctx, int enable);
 
+/* How the last nst_loss_grad ran (host only): *batches = block batches of Step 2 (each batch is
+ * every block that fits in the workspace at once); *resident = 1 when all blocks fitted in one
+ * batch, so one forward pass of every block (with the Step-2 margin) supplied both the Step-1
+ * statistics and the activations Step 2 back-propagates through, instead of a Step-1 pass with
+ * the smaller margin and a recomputed forward in Step 2 (Algorithm 1 as printed). Both give the
+ * same E and dE/dx up to summation order. Either pointer may be NULL. */
+nst_status nst_pass_info(nst_ctx *ctx, int *batches, int *resident);
+
 /* Synchronize `stream` and return (then clear) the latched device status. */
 nst_status nst_sync_status(nst_ctx *ctx, void *stream);
 

@@ -162,6 +162,8 @@ struct nst_ctx {
   size_t ctgt_cap = 0;
   int H = 0, W = 0, Hc = 0, Wc = 0;
   bool have_content = false;
+  bool resident = false;   // the last evaluation kept every block's activations (one forward)
+  int pass_batches = 0;    // Step-2 batches of the last evaluation
   // evaluation state
   double *d_gacc = nullptr, *d_gx = nullptr, *d_parts = nullptr, *d_loss = nullptr;
   void *d_R = nullptr;
@@ -694,8 +696,31 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   // Step 1: global statistics of x
   CK(cudaMemsetAsync(ctx->d_gacc, 0, sizeof(double) * kGramTotal, s));
   if (ctx->aug) CK(cudaMemsetAsync(ctx->d_sacc, 0, sizeof(double) * kMomentTotal, s));
-  nst_status st = stats_pass<T>(ctx, x, H, W, kPassStyleStats, s, ctx->aug);
+  PassPlan *p = nullptr;
+  nst_status st = build_plan(ctx, H, W, ctx->cfg.margin2, &p);
   if (st) return st;
+  Workspace ws;
+  st = ensure_buffers(ctx, *p, ws);
+  if (st) return st;
+  // Resident mode: when every block with the Step-2 margin fits in the workspace at once, one
+  // forward pass of all blocks serves both steps. The statistics come from the owned pixels of
+  // those blocks (exact, as the Step-2 margin exceeds Step 1's), and Step 2 back-propagates
+  // through the activations already in HBM instead of recomputing them.
+  const bool resident = p->batches.size() == 1;
+  ctx->resident = resident;
+  ctx->pass_batches = (int)p->batches.size();
+  if (resident) {
+    const Batch &bt = p->batches[0];
+    st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, s);
+    if (st) return st;
+    st = gram_batch<T>(ctx, *p, bt, ws, s, ctx->aug);
+    if (st) return st;
+  } else {
+    st = stats_pass<T>(ctx, x, H, W, kPassStyleStats, s, ctx->aug);
+    if (st) return st;
+    st = ensure_buffers(ctx, *p, ws);   // the Step-1 plan may have moved the workspace
+    if (st) return st;
+  }
   StyleFinalizeArgs fa{};
   for (int si = 0; si < kNStyle; si++) {
     const int stv = 1 << si;
@@ -724,16 +749,12 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   launch_style_finalize(fa, s);
   // Step 2: loss and gradient block by block
   CK(cudaMemsetAsync(ctx->d_parts + kNStyle, 0, sizeof(double), s));
-  PassPlan *p = nullptr;
-  st = build_plan(ctx, H, W, ctx->cfg.margin2, &p);
-  if (st) return st;
-  Workspace ws;
-  st = ensure_buffers(ctx, *p, ws);
-  if (st) return st;
   const int nt = (int)p->tiles.size();
   for (const Batch &bt : p->batches) {
-    st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, s);
-    if (st) return st;
+    if (!resident) {
+      st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, s);
+      if (st) return st;
+    }
     {
       Timer tm(ctx, kTOther, s);
       ctx->launches += 2;
@@ -1035,6 +1056,13 @@ nst_status nst_loss_grad_host(nst_ctx *ctx, const float *xh, int H, int W, float
   CK(cudaMemcpyAsync(gh, ctx->d_gh, n * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (lossh) CK(cudaMemcpyAsync(lossh, ctx->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return NST_OK;
+}
+
+nst_status nst_pass_info(nst_ctx *ctx, int *batches, int *resident) {
+  if (!ctx) return fail(nullptr, NST_ERR_INVALID_ARG, "null context");
+  if (batches) *batches = ctx->pass_batches;
+  if (resident) *resident = ctx->resident ? 1 : 0;
   return NST_OK;
 }
 

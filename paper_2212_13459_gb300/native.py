@@ -69,6 +69,8 @@ def lib():
                 "nst_get_timing": ([vp, dp, vp], ip),
                 "nst_set_timing": ([vp, ip], ip),
                 "nst_sync_status": ([vp, vp], ip),
+                "nst_pass_info": ([vp, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)], ip),
                 "nst_last_error": ([vp], ctypes.c_char_p),
                 "nst_tile_plan": ([ip, ip, ip, ip, ip, vp], ip),
                 "nst_lbfgs_create": ([ctypes.POINTER(vp), ll, ip], ip),
@@ -219,6 +221,12 @@ class Context:
 
     def sync_status(self, stream=None):
         return lib().nst_sync_status(self.h, _stream(stream))
+
+    def pass_info(self):
+        """(Step-2 batches, resident) of the last loss_grad call."""
+        b, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().nst_pass_info(self.h, ctypes.byref(b), ctypes.byref(r)), self.h)
+        return b.value, bool(r.value)
 
 
 def split_grams(flat):

@@ -68,6 +68,6 @@ def run_gpu(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, x=None, **cfg
     st = ctx.sync_status()
     parts, grams = ctx.stats()
     out = dict(E=float(loss.item()), g=grad.cpu().numpy().astype(np.float64), parts=parts,
-               grams=grams, style_grams=ctx.style_grams(), status=st)
+               grams=grams, style_grams=ctx.style_grams(), status=st, pass_info=ctx.pass_info())
     ctx.close()
     return out

@@ -38,6 +38,7 @@ typedef enum {
 
 enum { NST_PREC_FP32 = 0, NST_PREC_BF16 = 1 };
 enum { NST_CONV_AUTO = 0, NST_CONV_SIMT = 1, NST_CONV_TC = 2 };
+enum { NST_SCHED_AUTO = 0, NST_SCHED_TWO_PASS = 1 };
 
 /* Run-time configuration.
  *   w_style[5]: w_L of the Gram loss at ReLU1_1..ReLU5_1 (Section 3.1, Eq. 3).
@@ -58,7 +59,13 @@ enum { NST_CONV_AUTO = 0, NST_CONV_SIMT = 1, NST_CONV_TC = 2 };
  *   w_mean[5], w_std[5]: w'_L and w''_L of the augmented style loss (Section 3.2, Eq. 5):
  *               w'_L ||mean(V^L(x)) - mean(V^L(v))||^2 + w''_L ||std(V^L(x)) - std(V^L(v))||^2,
  *               population statistics over the image, std = (diag(G) - mean^2)^(1/2)
- *               (Algorithm 1, Step 1). 0 (the default) gives the plain Gram loss of Eq. 3. */
+ *               (Algorithm 1, Step 1). 0 (the default) gives the plain Gram loss of Eq. 3.
+ *   schedule:   NST_SCHED_TWO_PASS runs Algorithm 1 as printed: Step 1 forward with margin1,
+ *               then every block's forward again (with margin2) before its backward.
+ *               NST_SCHED_AUTO (the default) does the same unless every block of Step 2 fits in
+ *               the workspace at once; then one forward pass with margin2 supplies both the
+ *               statistics and the activations of the backward (resident; same E and dE/dx up
+ *               to summation order, a third less work). */
 typedef struct {
   float w_style[5];
   float lambda_c;
@@ -70,6 +77,7 @@ typedef struct {
   long long workspace_limit_bytes;
   float w_mean[5];
   float w_std[5];
+  int schedule;
 } nst_config;
 
 /* Fill *cfg with the defaults: w_style = 0.2 each, lambda_c = 1e-3, 1 x 1 tiles, margins 80/160,
@@ -130,6 +138,10 @@ nst_status nst_get_style_moments(nst_ctx *ctx, double *mean_host, double *std_ho
 nst_status nst_get_timing(nst_ctx *ctx, double *out6, void *stream);
 /* Enable or disable per-launch event timing; either way the counters restart from zero. */
 nst_status nst_set_timing(nst_ctx *ctx, int enable);
+
+/* Change the schedule of an existing context (NST_SCHED_AUTO or NST_SCHED_TWO_PASS, see
+ * nst_config); applies from the next nst_loss_grad. */
+nst_status nst_set_schedule(nst_ctx *ctx, int schedule);
 
 /* How the last nst_loss_grad ran (host only): *batches = block batches of Step 2 (each batch is
  * every block that fits in the workspace at once); *resident = 1 when all blocks fitted in one

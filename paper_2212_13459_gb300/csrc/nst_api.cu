@@ -706,7 +706,7 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   // forward pass of all blocks serves both steps. The statistics come from the owned pixels of
   // those blocks (exact, as the Step-2 margin exceeds Step 1's), and Step 2 back-propagates
   // through the activations already in HBM instead of recomputing them.
-  const bool resident = p->batches.size() == 1;
+  const bool resident = p->batches.size() == 1 && ctx->cfg.schedule != NST_SCHED_TWO_PASS;
   ctx->resident = resident;
   ctx->pass_batches = (int)p->batches.size();
   if (resident) {
@@ -844,7 +844,8 @@ nst_status nst_create(nst_ctx **out, const float *params, long long n_params,
   if (cfg->tiles_h < 1 || cfg->tiles_w < 1 || cfg->margin1 < 0 || cfg->margin2 < 0 ||
       cfg->margin1 % 16 || cfg->margin2 % 16 ||
       (cfg->precision != NST_PREC_FP32 && cfg->precision != NST_PREC_BF16) ||
-      cfg->conv_engine < 0 || cfg->conv_engine > 2 || cfg->max_batch_tiles < 0)
+      cfg->conv_engine < 0 || cfg->conv_engine > 2 || cfg->max_batch_tiles < 0 ||
+      cfg->schedule < 0 || cfg->schedule > 1)
     return fail(nullptr, NST_ERR_INVALID_ARG, "invalid configuration");
   if (cfg->conv_engine == NST_CONV_TC && cfg->precision != NST_PREC_BF16)
     return fail(nullptr, NST_ERR_INVALID_ARG, "the tensor-core engine needs BF16 precision");
@@ -1056,6 +1057,13 @@ nst_status nst_loss_grad_host(nst_ctx *ctx, const float *xh, int H, int W, float
   CK(cudaMemcpyAsync(gh, ctx->d_gh, n * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (lossh) CK(cudaMemcpyAsync(lossh, ctx->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  return NST_OK;
+}
+
+nst_status nst_set_schedule(nst_ctx *ctx, int schedule) {
+  if (!ctx) return fail(nullptr, NST_ERR_INVALID_ARG, "null context");
+  if (schedule < 0 || schedule > 1) return fail(ctx, NST_ERR_INVALID_ARG, "unknown schedule");
+  ctx->cfg.schedule = schedule;
   return NST_OK;
 }
 

@@ -21,6 +21,7 @@ NST_OK, NST_ERR_INVALID_ARG, NST_ERR_SHAPE, NST_ERR_CUDA, NST_ERR_OOM = 0, 1, 2,
 NST_ERR_TIMEOUT, NST_ERR_NONFINITE, NST_ERR_STATE = 5, 6, 7
 PREC_FP32, PREC_BF16 = 0, 1
 CONV_AUTO, CONV_SIMT, CONV_TC = 0, 1, 2
+SCHED_AUTO, SCHED_TWO_PASS = 0, 1
 N_PARAMS = 12944960
 GRAM_TOTAL = 610304
 STYLE_CHANNELS = [64, 128, 256, 512, 512]
@@ -41,7 +42,8 @@ class Config(ctypes.Structure):
                 ("margin1", ctypes.c_int), ("margin2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("conv_engine", ctypes.c_int),
                 ("max_batch_tiles", ctypes.c_int), ("workspace_limit_bytes", ctypes.c_longlong),
-                ("w_mean", ctypes.c_float * 5), ("w_std", ctypes.c_float * 5)]
+                ("w_mean", ctypes.c_float * 5), ("w_std", ctypes.c_float * 5),
+                ("schedule", ctypes.c_int)]
 
 
 def lib():
@@ -69,6 +71,7 @@ def lib():
                 "nst_get_timing": ([vp, dp, vp], ip),
                 "nst_set_timing": ([vp, ip], ip),
                 "nst_sync_status": ([vp, vp], ip),
+                "nst_set_schedule": ([vp, ip], ip),
                 "nst_pass_info": ([vp, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int)], ip),
                 "nst_last_error": ([vp], ctypes.c_char_p),
@@ -221,6 +224,9 @@ class Context:
 
     def sync_status(self, stream=None):
         return lib().nst_sync_status(self.h, _stream(stream))
+
+    def set_schedule(self, schedule):
+        _check(lib().nst_set_schedule(self.h, int(schedule)), self.h)
 
     def pass_info(self):
         """(Step-2 batches, resident) of the last loss_grad call."""

@@ -148,15 +148,18 @@ def test_call_order_and_shape_errors():
     assert e.value.code == native.NST_ERR_SHAPE
 
 
+@pytest.mark.parametrize("two_pass,expect", [(dict(max_batch_tiles=1), (4, False)),
+                                             (dict(schedule=native.SCHED_TWO_PASS), (1, False))])
 @pytest.mark.parametrize("name,cfg", [("fp32", FP32),
                                       ("bf16-tc", dict(precision=native.PREC_BF16,
                                                        conv_engine=native.CONV_TC))])
-def test_resident_and_two_pass_agree(name, cfg):
-    """All blocks in one batch (one forward pass supplies both steps) against one block per
-    batch (Step-1 pass with margin 80, forward recomputed in Step 2, Algorithm 1 as printed)."""
+def test_resident_and_two_pass_agree(name, cfg, two_pass, expect):
+    """All blocks in one batch (one forward pass supplies both steps) against Algorithm 1 as
+    printed (Step-1 pass with margin 80, forward recomputed in Step 2), with one block per batch
+    or with every block in one batch."""
     a = run_gpu(96, 128, 4, tiles_h=2, tiles_w=2, **cfg)
-    b = run_gpu(96, 128, 4, tiles_h=2, tiles_w=2, max_batch_tiles=1, **cfg)
-    assert a["pass_info"] == (1, True) and b["pass_info"] == (4, False)
+    b = run_gpu(96, 128, 4, tiles_h=2, tiles_w=2, **two_pass, **cfg)
+    assert a["pass_info"] == (1, True) and b["pass_info"] == expect
     assert a["status"] == 0 and b["status"] == 0
     for s in range(5):
         assert rel_l2(a["grams"][s], b["grams"][s]) <= (1e-6 if name == "fp32" else 2e-3)

@@ -408,7 +408,8 @@ def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev):
     from paper_2212_13459_gb300 import native
     ctx = native.Context(flat, tiles_h=k, tiles_w=k, precision=native.PREC_FP32,
                          margin1=args.margin1, margin2=args.margin2,
-                         workspace_limit_bytes=int(args.workspace_gb * 1e9))
+                         workspace_limit_bytes=int(args.workspace_gb * 1e9),
+                         schedule=native.SCHED_TWO_PASS)
     ctx.style_targets(v)
     ctx.content_targets(u)
     g32 = torch.empty_like(x)

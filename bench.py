@@ -46,6 +46,23 @@ WORKLOADS = {
 }
 
 
+def max_over_ranks(v, dist, dev):
+    """The slowest rank's time: every rank gets the maximum of v over the process group
+    (identity without one)."""
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([float(v)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpx_s(world, H, W, steps, seconds):
+    """Replicas: every rank evaluates its own H x W image `steps` times; the job's throughput is
+    all ranks' pixels over the slowest rank's time."""
+    return world * H * W * steps / seconds / 1e6
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -233,13 +250,11 @@ def run_ours(args, rank, world, local_rank):
     tm = ctx.timing()
     ctx.set_timing(False)
     clk = clocks.stop()
+    ms = max_over_ranks(ms, dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_step = ms / args.steps
-    value = world * H * W * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_mpx_s(world, H, W, args.steps, ms / 1e3)
     E = float(loss.item())
     status = ctx.sync_status()
 
@@ -274,12 +289,8 @@ def e2e_leg(ctx, x, H, W, args, dist, dev, world):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.loss_grad_host(xh_np, gh_np)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    return {"value": world * H * W * e2e_steps / e2e_s / 1e6, "unit": "Mpx/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    return {"value": whole_job_mpx_s(world, H, W, e2e_steps, e2e_s), "unit": "Mpx/s",
             "h2d_bytes_per_step": 3 * H * W * 4, "d2h_bytes_per_step": 3 * H * W * 4 + 8,
             "steps": e2e_steps}
 
@@ -327,14 +338,10 @@ def resident_leg(ctx, x, grad, loss, H, W, args, stream, dev, dist, world):
         ctx.loss_grad(x, grad, loss)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     batches, resident = ctx.pass_info()
     ctx.set_schedule(native.SCHED_TWO_PASS)
-    return {"value": world * H * W * args.steps / (ms / 1e3) / 1e6, "unit": "Mpx/s",
+    return {"value": whole_job_mpx_s(world, H, W, args.steps, ms / 1e3), "unit": "Mpx/s",
             "ms_per_step": ms / args.steps, "resident": resident, "step2_batches": batches,
             "loss": float(loss.item())}
 

@@ -526,6 +526,87 @@ constexpr uint32_t kSwapA = kSwapBN * kBK * 2;  // 16 KB weight box
 constexpr uint32_t kSwapB = kSwapBP * kBK * 2;  // 32 KB activation box
 constexpr uint32_t kSwapT = 32 * 32 * 4;        // transpose tile per epilogue warp
 
+// 8 consecutive channels (group cg) of chunk pixel j from the warp's transpose tile (row j,
+// logical 16-byte chunks 2cg and 2cg + 1, stored at chunk ^ (j % 8))
+__device__ __forceinline__ void swap_tile_read8(const uint8_t *tsm, int j, int cg, float *r) {
+  const float4 f0 = *reinterpret_cast<const float4 *>(tsm + j * 128 + (((2 * cg) ^ (j & 7)) << 4));
+  const float4 f1 =
+      *reinterpret_cast<const float4 *>(tsm + j * 128 + (((2 * cg + 1) ^ (j & 7)) << 4));
+  r[0] = f0.x; r[1] = f0.y; r[2] = f0.z; r[3] = f0.w;
+  r[4] = f1.x; r[5] = f1.y; r[6] = f1.z; r[7] = f1.w;
+}
+
+// epilogue32 for 8 channels n .. n+7 of one pixel (no content term)
+__device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g, int b, int y,
+                                          int x, int n, float *v) {
+  const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
+  const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
+  if (a.mode == kEpiForward) {
+    const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n));
+    const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + 4));
+    const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = valid ? fmaxf(v[j] + bb[j], 0.f) : 0.f;
+  } else if (!valid) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = 0.f;
+  } else {
+    if (a.addvec) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) v[j] += __ldg(a.addvec + n + j);
+    }
+    if (a.mask) {
+      float m8[8];
+      ld_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(a.mask) + o, m8);
+#pragma unroll
+      for (int j = 0; j < 8; j++) v[j] = m8[j] > 0.f ? v[j] : 0.f;
+    }
+  }
+  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.out) + o, v);
+}
+
+// fused 2 x 2 max pool of a 32-pixel chunk (whole rows of a patch 8 or 16 wide) from the warp's
+// transpose tile: lane = (window, 8-channel group); the window's four values are recomputed
+// exactly as the forward epilogue stored them (bias, ReLU, valid region, BF16 rounding)
+__device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g, int b, int tx,
+                                           int ty, const TcGeom &tg, int c, int n,
+                                           const uint8_t *tsm) {
+  const int lane = threadIdx.x & 31;
+  const int w = lane >> 2, cg = lane & 3;
+  const int wpr = tg.TW >> 1;   // windows per row pair
+  const int j0 = 2 * (w / wpr) * tg.TW + 2 * (w % wpr);
+  const int pp0 = c + j0;
+  const int y = ty * tg.TH + pp0 / tg.TW, x = tx * tg.TW + pp0 % tg.TW;
+  if (pp0 >= tg.TH * tg.TW || y >= a.Hb || x >= a.Wb) return;
+  const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8));
+  const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8 + 4));
+  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
+  float m[8];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int j = j0 + (q >> 1) * tg.TW + (q & 1);
+    const bool valid = y + (q >> 1) < ehl && x + (q & 1) < ewl;
+    float r[8];
+    swap_tile_read8(tsm, j, cg, r);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const float s = __bfloat162float(__float2bfloat16_rn(valid ? fmaxf(r[i] + bb[i], 0.f)
+                                                                 : 0.f));
+      m[i] = q == 0 ? s : fmaxf(m[i], s);
+    }
+  }
+  const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
+  const bool pv = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
+  if (!pv) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) m[i] = 0.f;
+  }
+  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + (((size_t)b * Hp + py) * Wp + px) *
+                                                                 a.cout + n + cg * 8,
+            m);
+}
+
 template <int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_swap_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -659,27 +740,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           *reinterpret_cast<float *>(tsm + j * 128 + ((((lane >> 2) ^ (j & 7)) << 4) |
                                                       ((lane & 3) << 2))) = v[j];
         __syncwarp();
+        // read back four lanes per pixel (8 channels each): every 16-byte store of the warp then
+        // covers 8 pixels x 64 contiguous bytes
+        const int cg = lane & 3;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const float4 f = *reinterpret_cast<const float4 *>(tsm + lane * 128 +
-                                                             ((k ^ (lane & 7)) << 4));
-          v[4 * k] = f.x;
-          v[4 * k + 1] = f.y;
-          v[4 * k + 2] = f.z;
-          v[4 * k + 3] = f.w;
+        for (int k = 0; k < 4; k++) {
+          const int j = k * 8 + (lane >> 2);   // pixel of the chunk
+          float r[8];
+          swap_tile_read8(tsm, j, cg, r);
+          const int pp = c + j;
+          const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
+          if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb) epilogue8(a, g, b, y, x, n + cg * 8, r);
         }
+        if (a.pool_out) swap_pool8(a, g, b, tx, ty, tg, c, n, tsm);
         __syncwarp();
-        const int pp = c + lane;   // this lane's pixel of the patch, channels n .. n+31 in v
-        const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
-        const bool inb = pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb;
-        if (inb) epilogue32(a, g, b, y, x, n, v);
-        if (a.pool_out) {
-          if (!inb) {
-#pragma unroll
-            for (int j = 0; j < 32; j++) v[j] = 0.f;
-          }
-          pool_epilogue32(a, g, b, y, x, n, tg.TW, v);
-        }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
@@ -898,7 +972,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   int hBN, hKB, hP2, hNT;
   if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
   // 128 output channels: pixels as the MMA's N (256 wide) instead of channels (128 wide)
-  const bool swap = a.cout == kSwapBN;
+  const bool swap = a.cout == kSwapBN && !a.cact;   // (its epilogue has no content term)
   const int BN = swap ? kSwapBN : (a.cout >= 256 ? 256 : a.cout);
   TcGeom tg;
   pick_patch_rows(a.Hb, a.Wb, swap ? kSwapBP : 128, tg.TH, tg.TW, a.pool_out != nullptr);

@@ -164,6 +164,105 @@ __device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGe
                    : make_uint4(0u, 0u, 0u, 0u);
 }
 
+// ---- epilogue through a per-warp transpose tile -----------------------------------------------------
+// A warp's 32 x 32 chunk (pixels x channels, FP32) goes to a 4 KB shared-memory tile (row =
+// pixel, 16-byte chunks XOR-swizzled by row) and comes back four lanes per pixel, 8 channels
+// each: a 16-byte store instruction then covers 8 pixels x 64 contiguous bytes instead of 32
+// pixels x 16 bytes at the pixel stride.
+constexpr uint32_t kTileT = 32 * 32 * 4;
+
+// 8 consecutive channels (group cg) of chunk pixel j from the warp's transpose tile (row j,
+// logical 16-byte chunks 2cg and 2cg + 1, stored at chunk ^ (j % 8))
+__device__ __forceinline__ void swap_tile_read8(const uint8_t *tsm, int j, int cg, float *r) {
+  const float4 f0 = *reinterpret_cast<const float4 *>(tsm + j * 128 + (((2 * cg) ^ (j & 7)) << 4));
+  const float4 f1 =
+      *reinterpret_cast<const float4 *>(tsm + j * 128 + (((2 * cg + 1) ^ (j & 7)) << 4));
+  r[0] = f0.x; r[1] = f0.y; r[2] = f0.z; r[3] = f0.w;
+  r[4] = f1.x; r[5] = f1.y; r[6] = f1.z; r[7] = f1.w;
+}
+
+// epilogue32 for 8 channels n .. n+7 of one pixel
+__device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g, int b, int y,
+                                          int x, int n, float *v) {
+  const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
+  const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
+  if (a.mode == kEpiForward) {
+    const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n));
+    const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + 4));
+    const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = valid ? fmaxf(v[j] + bb[j], 0.f) : 0.f;
+  } else if (!valid) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = 0.f;
+  } else {
+    if (a.cact) {
+      const int gy = (g.ey0 >> a.level) + y, gx = (g.ex0 >> a.level) + x;
+      if (gy < a.Hc && gx < a.Wc) {
+        float c8[8], t8[8];
+        ld_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(a.cact) + o, c8);
+        ld_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(a.ctgt) +
+                      ((size_t)gy * a.Wc + gx) * a.cout + n, t8);
+#pragma unroll
+        for (int j = 0; j < 8; j++) v[j] += a.two_lambda * (c8[j] - t8[j]);
+      }
+    }
+    if (a.addvec) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) v[j] += __ldg(a.addvec + n + j);
+    }
+    if (a.mask) {
+      float m8[8];
+      ld_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(a.mask) + o, m8);
+#pragma unroll
+      for (int j = 0; j < 8; j++) v[j] = m8[j] > 0.f ? v[j] : 0.f;
+    }
+  }
+  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.out) + o, v);
+}
+
+// fused 2 x 2 max pool of a 32-pixel chunk (whole rows of a patch 8 or 16 wide) from the warp's
+// transpose tile: lane = (window, 8-channel group); the window's four values are recomputed
+// exactly as the forward epilogue stored them (bias, ReLU, valid region, BF16 rounding)
+__device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g, int b, int tx,
+                                           int ty, const TcGeom &tg, int c, int n,
+                                           const uint8_t *tsm) {
+  const int lane = threadIdx.x & 31;
+  const int w = lane >> 2, cg = lane & 3;
+  const int wpr = tg.TW >> 1;   // windows per row pair
+  const int j0 = 2 * (w / wpr) * tg.TW + 2 * (w % wpr);
+  const int pp0 = c + j0;
+  const int y = ty * tg.TH + pp0 / tg.TW, x = tx * tg.TW + pp0 % tg.TW;
+  if (pp0 >= tg.TH * tg.TW || y >= a.Hb || x >= a.Wb) return;
+  const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8));
+  const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8 + 4));
+  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
+  float m[8];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int j = j0 + (q >> 1) * tg.TW + (q & 1);
+    const bool valid = y + (q >> 1) < ehl && x + (q & 1) < ewl;
+    float r[8];
+    swap_tile_read8(tsm, j, cg, r);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const float s = __bfloat162float(__float2bfloat16_rn(valid ? fmaxf(r[i] + bb[i], 0.f)
+                                                                 : 0.f));
+      m[i] = q == 0 ? s : fmaxf(m[i], s);
+    }
+  }
+  const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
+  const bool pv = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
+  if (!pv) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) m[i] = 0.f;
+  }
+  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + (((size_t)b * Hp + py) * Wp + px) *
+                                                                 a.cout + n + cg * 8,
+            m);
+}
+
 // ---- the kernel -------------------------------------------------------------------------------------
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -274,7 +373,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..5) ----------------
     const int q = warp & 3;           // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2; // which half of the accumulator columns it drains
-    const int row = q * 32 + lane;    // M row = pixel of the patch
+    uint8_t *tsm = smem_raw + ((smem_base - smem_u32(smem_raw)) + STAGES * STAGE_BYTES +
+                               (size_t)(warp - 2) * kTileT);
     int it = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
@@ -284,22 +384,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
       const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
       const int b = mt / (tg.tiles_x * tg.tiles_y);
-      const int y = ty * tg.TH + row / tg.TW, x = tx * tg.TW + row % tg.TW;
-      const bool inb = row < tg.TH * tg.TW && y < a.Hb && x < a.Wb;
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      const int cg = lane & 3;
 #pragma unroll 1
       for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
-        tmem_ld32(tbase + (uint32_t)c, v);
-        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
-        if (a.pool_out) {
-          if (!inb) {
+        tmem_ld32(tbase + (uint32_t)c, v);   // row = this lane's pixel, 32 channels
 #pragma unroll
-            for (int j = 0; j < 32; j++) v[j] = 0.f;
+        for (int k = 0; k < 8; k++)
+          *reinterpret_cast<float4 *>(tsm + lane * 128 + ((k ^ (lane & 7)) << 4)) =
+              make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int j = k * 8 + (lane >> 2);
+          const int pp = q * 32 + j;
+          const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
+          if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb) {
+            float r[8];
+            swap_tile_read8(tsm, j, cg, r);
+            epilogue8(a, g, b, y, x, nt * BN + c + cg * 8, r);
           }
-          pool_epilogue32(a, g, b, y, x, nt * BN + c, tg.TW, v);
         }
+        if (a.pool_out) swap_pool8(a, g, b, tx, ty, tg, q * 32, nt * BN + c, tsm);
+        __syncwarp();
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
@@ -524,88 +633,6 @@ constexpr int kSwapBN = 128;                    // output channels per tile (M)
 constexpr int kSwapBP = 256;                    // output pixels per tile (N)
 constexpr uint32_t kSwapA = kSwapBN * kBK * 2;  // 16 KB weight box
 constexpr uint32_t kSwapB = kSwapBP * kBK * 2;  // 32 KB activation box
-constexpr uint32_t kSwapT = 32 * 32 * 4;        // transpose tile per epilogue warp
-
-// 8 consecutive channels (group cg) of chunk pixel j from the warp's transpose tile (row j,
-// logical 16-byte chunks 2cg and 2cg + 1, stored at chunk ^ (j % 8))
-__device__ __forceinline__ void swap_tile_read8(const uint8_t *tsm, int j, int cg, float *r) {
-  const float4 f0 = *reinterpret_cast<const float4 *>(tsm + j * 128 + (((2 * cg) ^ (j & 7)) << 4));
-  const float4 f1 =
-      *reinterpret_cast<const float4 *>(tsm + j * 128 + (((2 * cg + 1) ^ (j & 7)) << 4));
-  r[0] = f0.x; r[1] = f0.y; r[2] = f0.z; r[3] = f0.w;
-  r[4] = f1.x; r[5] = f1.y; r[6] = f1.z; r[7] = f1.w;
-}
-
-// epilogue32 for 8 channels n .. n+7 of one pixel (no content term)
-__device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g, int b, int y,
-                                          int x, int n, float *v) {
-  const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
-  const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
-  if (a.mode == kEpiForward) {
-    const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n));
-    const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + 4));
-    const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = valid ? fmaxf(v[j] + bb[j], 0.f) : 0.f;
-  } else if (!valid) {
-#pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = 0.f;
-  } else {
-    if (a.addvec) {
-#pragma unroll
-      for (int j = 0; j < 8; j++) v[j] += __ldg(a.addvec + n + j);
-    }
-    if (a.mask) {
-      float m8[8];
-      ld_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(a.mask) + o, m8);
-#pragma unroll
-      for (int j = 0; j < 8; j++) v[j] = m8[j] > 0.f ? v[j] : 0.f;
-    }
-  }
-  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.out) + o, v);
-}
-
-// fused 2 x 2 max pool of a 32-pixel chunk (whole rows of a patch 8 or 16 wide) from the warp's
-// transpose tile: lane = (window, 8-channel group); the window's four values are recomputed
-// exactly as the forward epilogue stored them (bias, ReLU, valid region, BF16 rounding)
-__device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g, int b, int tx,
-                                           int ty, const TcGeom &tg, int c, int n,
-                                           const uint8_t *tsm) {
-  const int lane = threadIdx.x & 31;
-  const int w = lane >> 2, cg = lane & 3;
-  const int wpr = tg.TW >> 1;   // windows per row pair
-  const int j0 = 2 * (w / wpr) * tg.TW + 2 * (w % wpr);
-  const int pp0 = c + j0;
-  const int y = ty * tg.TH + pp0 / tg.TW, x = tx * tg.TW + pp0 % tg.TW;
-  if (pp0 >= tg.TH * tg.TW || y >= a.Hb || x >= a.Wb) return;
-  const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8));
-  const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8 + 4));
-  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-  const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
-  float m[8];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int j = j0 + (q >> 1) * tg.TW + (q & 1);
-    const bool valid = y + (q >> 1) < ehl && x + (q & 1) < ewl;
-    float r[8];
-    swap_tile_read8(tsm, j, cg, r);
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const float s = __bfloat162float(__float2bfloat16_rn(valid ? fmaxf(r[i] + bb[i], 0.f)
-                                                                 : 0.f));
-      m[i] = q == 0 ? s : fmaxf(m[i], s);
-    }
-  }
-  const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
-  const bool pv = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
-  if (!pv) {
-#pragma unroll
-    for (int i = 0; i < 8; i++) m[i] = 0.f;
-  }
-  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + (((size_t)b * Hp + py) * Wp + px) *
-                                                                 a.cout + n + cg * 8,
-            m);
-}
 
 template <int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -717,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..9) ----------------
     const int q = warp & 3;            // TMEM lane quarter = channels q*32 .. q*32+31 of the tile
     const int half = (warp - 2) >> 2;  // pixels half*128 .. half*128+127 of the patch
-    uint8_t *tsm = smem_gen + STAGES * STAGE_BYTES + (size_t)(warp - 2) * kSwapT;
+    uint8_t *tsm = smem_gen + STAGES * STAGE_BYTES + (size_t)(warp - 2) * kTileT;
     int it = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
@@ -826,7 +853,8 @@ template <int BN, int STAGES>
 cudaError_t launch_bn(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                       const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
                       cudaStream_t s) {
-  constexpr size_t smem = (size_t)STAGES * (128 * kBK * 2 + BN * kBK * 2) + 1024;
+  constexpr size_t smem = (size_t)STAGES * (128 * kBK * 2 + BN * kBK * 2) + 8 * kTileT + 1024;
+  static_assert(smem <= 227 * 1024, "tcgen05 convolution shared memory");
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>,
@@ -843,7 +871,7 @@ template <int STAGES>
 cudaError_t launch_swap(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, const TcGeom &tg,
                         cudaStream_t s) {
-  constexpr size_t smem = (size_t)STAGES * (kSwapA + kSwapB) + 8 * kSwapT + 1024;
+  constexpr size_t smem = (size_t)STAGES * (kSwapA + kSwapB) + 8 * kTileT + 1024;
   static_assert(smem <= 227 * 1024, "pixels-as-N kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
@@ -972,7 +1000,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   int hBN, hKB, hP2, hNT;
   if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
   // 128 output channels: pixels as the MMA's N (256 wide) instead of channels (128 wide)
-  const bool swap = a.cout == kSwapBN && !a.cact;   // (its epilogue has no content term)
+  const bool swap = a.cout == kSwapBN;
   const int BN = swap ? kSwapBN : (a.cout >= 256 ? 256 : a.cout);
   TcGeom tg;
   pick_patch_rows(a.Hb, a.Wb, swap ? kSwapBP : 128, tg.TH, tg.TW, a.pool_out != nullptr);

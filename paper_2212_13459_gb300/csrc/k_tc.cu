@@ -440,11 +440,9 @@ template <int BN, int KB, int P2KB, int NT>
 struct HaloCfg {
   static constexpr uint32_t TILE_B = BN * 128;                  // one (tap, K-block) weight tile
   static constexpr uint32_t W_BYTES = (9 * KB + P2KB) * TILE_B;
-  static constexpr int STAGES_RAW =
-      (int)((kHaloSmemMax - 1024 - W_BYTES - 8 * kTileT) / kHaloStage);
+  static constexpr int STAGES_RAW = (int)((kHaloSmemMax - 1024 - W_BYTES) / kHaloStage);
   static constexpr int STAGES = STAGES_RAW > 4 ? 4 : STAGES_RAW;
-  static constexpr size_t TILE_OFF = W_BYTES + (size_t)STAGES * kHaloStage;   // transpose tiles
-  static constexpr size_t SMEM = 1024 + TILE_OFF + 8 * kTileT;
+  static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloStage;
 };
 
 template <int BN, int KB, int P2KB, int NT>
@@ -584,9 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
-    uint8_t *tsm = smem_raw + ((smem_base - smem_u32(smem_raw)) + Cfg::TILE_OFF +
-                               (size_t)(warp - 2) * kTileT);
-    const int cg = lane & 3;
+    const int row = q * 32 + lane;
     int it = 0;
     for (int t = m_first; t < m_total; t += m_step, it++) {
       const int acc = it % NACC;
@@ -595,30 +591,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
       const int b = t / (tg.tiles_x * tg.tiles_y);
+      const int y = ty * kHaloTH + row / kHaloTW, x = tx * kHaloTW + row % kHaloTW;
+      const bool inb = y < a.Hb && x < a.Wb;
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
       for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
-        tmem_ld32(tbase + (uint32_t)c, v);   // row = this lane's pixel, 32 channels
+        tmem_ld32(tbase + (uint32_t)c, v);
+        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
+        if (a.pool_out) {
+          if (!inb) {
 #pragma unroll
-        for (int k = 0; k < 8; k++)
-          *reinterpret_cast<float4 *>(tsm + lane * 128 + ((k ^ (lane & 7)) << 4)) =
-              make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const int j = k * 8 + (lane >> 2);
-          const int pp = q * 32 + j;
-          const int y = ty * kHaloTH + pp / kHaloTW, x = tx * kHaloTW + pp % kHaloTW;
-          if (y < a.Hb && x < a.Wb) {
-            float r[8];
-            swap_tile_read8(tsm, j, cg, r);
-            epilogue8(a, g, b, y, x, nt * BN + c + cg * 8, r);
+            for (int j = 0; j < 32; j++) v[j] = 0.f;
           }
+          pool_epilogue32(a, g, b, y, x, nt * BN + c, kHaloTW, v);
         }
-        if (a.pool_out) swap_pool8(a, g, b, tx, ty, tg, q * 32, nt * BN + c, tsm);
-        __syncwarp();
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));

@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
   } else {
     const int q = warp & 3;
     const int row = q * 32 + lane;   // channel I * 128 + row
-    if (mbar_wait(smem_u32(&done_bar), 0, &abort_flag, a.err)) {
+    // lane 0 waits (bounded); the warp then proceeds or leaves as one (tcgen05.ld is warp-wide)
+    int ready = 0;
+    if (lane == 0) ready = mbar_wait(smem_u32(&done_bar), 0, &abort_flag, a.err);
+    if (__shfl_sync(0xffffffffu, ready, 0)) {
       tc_fence_after();
       float *out = a.part + (((size_t)blockIdx.x * a.nI * a.nJ + tile) * 128 + row) * N;
       const bool live = I * 128 + row < a.C;

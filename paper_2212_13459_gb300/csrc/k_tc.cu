@@ -240,7 +240,10 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
   const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
   float m[8];
 #pragma unroll
-  for (int q = 0; q < 4; q++) {
+  for (int qq = 0; qq < 4; qq++) {
+    // odd windows visit their pixels in the order 1, 0, 3, 2: the two windows of a quarter-warp
+    // then read rows of opposite parity, whose swizzled chunks fall on different banks
+    const int q = qq ^ (w & 1);
     const int j = j0 + (q >> 1) * tg.TW + (q & 1);
     const bool valid = y + (q >> 1) < ehl && x + (q & 1) < ewl;
     float r[8];
@@ -249,7 +252,7 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
     for (int i = 0; i < 8; i++) {
       const float s = __bfloat162float(__float2bfloat16_rn(valid ? fmaxf(r[i] + bb[i], 0.f)
                                                                  : 0.f));
-      m[i] = q == 0 ? s : fmaxf(m[i], s);
+      m[i] = qq == 0 ? s : fmaxf(m[i], s);
     }
   }
   const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; i++) {
       mbar_init(smem_u32(&tfull_bar[i]), 1);
-      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads);
+      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads / 32);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -379,7 +382,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      // lane 0 waits (bounded) and the warp leaves together: the epilogue's warp-wide
+      // shuffles and __syncwarp need every lane
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err);
+      if (!__shfl_sync(0xffffffffu, ready, 0)) break;
       tc_fence_after();
       const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
       const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
@@ -411,7 +418,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
       }
       tc_fence_before();
-      mbar_arrive(smem_u32(&tempty_bar[acc]));
+      __syncwarp();   // every lane of the warp has finished its TMEM reads
+      if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
     }
   }
   tc_fence_before();
@@ -587,7 +595,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = m_first; t < m_total; t += m_step, it++) {
       const int acc = it % NACC;
       const uint32_t use = (uint32_t)(it / NACC);
-      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      // lane 0 waits (bounded) and the warp leaves together: the epilogue's warp-wide
+      // shuffles and __syncwarp need every lane
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err);
+      if (!__shfl_sync(0xffffffffu, ready, 0)) break;
       tc_fence_after();
       const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
       const int b = t / (tg.tiles_x * tg.tiles_y);
@@ -662,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; i++) {
       mbar_init(smem_u32(&tfull_bar[i]), 1);
-      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads);
+      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads / 32);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -749,7 +761,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err)) break;
+      // lane 0 waits (bounded) and the warp leaves together: the epilogue's warp-wide
+      // shuffles and __syncwarp need every lane
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err);
+      if (!__shfl_sync(0xffffffffu, ready, 0)) break;
       tc_fence_after();
       const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
       const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
@@ -783,7 +799,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
       }
       tc_fence_before();
-      mbar_arrive(smem_u32(&tempty_bar[acc]));
+      __syncwarp();   // every lane of the warp has finished its TMEM reads
+      if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
     }
   }
   tc_fence_before();

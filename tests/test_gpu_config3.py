@@ -1,0 +1,65 @@
+"""The scale-1 configuration of the multiscale pyramid at the paper's shape: content 756 x 1008,
+style 1057 x 1330 stroke texture. The gradient of the autograd wrapper against central finite
+differences (h = 1e-3) at 64 pixels, and 300 L-BFGS iterations with the BF16 tensor-core form."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2212_13459_gb300 import driver, native, synth
+
+pytestmark = pytest.mark.gpu
+
+H, W, HV, WV, SEED = 756, 1008, 1057, 1330, 2
+
+
+def _setup(**cfg):
+    params = synth.vgg19_params(SEED)
+    u = torch.from_numpy(synth.content_image(H, W, SEED)).cuda()
+    v = torch.from_numpy(synth.stroke_style(HV, WV, SEED)).cuda()
+    ctx = native.Context(synth.flat_params(params), **cfg)
+    ctx.style_targets(v)
+    ctx.content_targets(u)
+    return ctx, u
+
+
+def test_config3_gradient_matches_central_differences_at_64_pixels():
+    """FP32 form: per-pixel central differences of E at h = 1e-3 against the library's dE/dx.
+    The loss is piecewise smooth (ReLU and pooling kinks), so the 64 differences are compared
+    as a vector (relative L2, 5e-2) and pixel by pixel against the vector's scale."""
+    ctx, u = _setup(precision=native.PREC_FP32)
+    x = torch.clamp(u + 0.05 * torch.randn(u.shape, device="cuda",
+                                           generator=torch.Generator("cuda").manual_seed(0)),
+                    0, 1).contiguous()
+    xr = x.clone().requires_grad_(True)
+    driver.nst_loss(xr, ctx).backward()
+    g = xr.grad.double()
+    rng = np.random.default_rng(3)
+    idx = [(int(rng.integers(3)), int(rng.integers(8, H - 8)), int(rng.integers(8, W - 8)))
+           for _ in range(64)]
+    h = 1e-3
+    fd, an = [], []
+    for c, y, xx in idx:
+        xp = x.clone()
+        xp[c, y, xx] += h
+        xm = x.clone()
+        xm[c, y, xx] -= h
+        fd.append((driver.nst_loss(xp, ctx).item() - driver.nst_loss(xm, ctx).item()) / (2 * h))
+        an.append(float(g[c, y, xx]))
+    fd, an = np.array(fd), np.array(an)
+    assert np.linalg.norm(fd - an) <= 5e-2 * np.linalg.norm(an)
+    assert np.abs(fd - an).max() <= 0.2 * np.abs(an).max()
+    ctx.close()
+
+
+def test_config3_lbfgs_300_iterations_bf16():
+    ctx, u = _setup(precision=native.PREC_BF16)
+    x = u.clone()
+    losses = []
+    driver.style_transfer(ctx, x, 300, history=100,
+                          callback=lambda k, l: losses.append(l.item()) if k % 50 == 0 or
+                          k == 299 else None)
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.2 * losses[0], losses
+    assert torch.isfinite(x).all()
+    assert ctx.sync_status() == 0
+    ctx.close()

@@ -1,0 +1,44 @@
+"""The 512 x 512 configuration (content and style from the small-config generators, seed 1):
+untiled against 4 x 4 blocks in both forms, and 100 L-BFGS iterations (history 10) with the BF16
+tensor-core form. Per-layer Gram, loss and gradient errors against the FP64 oracle are the
+128 x 128 cases of test_gpu_parity.py."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2212_13459_gb300 import driver, native
+from tests._gpu import TOL_BF16_FULL_GRAD, rel_l2, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,cfg,tol,gtol", [
+    ("fp32", dict(precision=native.PREC_FP32), 1e-5, 1e-2),
+    ("bf16", dict(precision=native.PREC_BF16), 2e-3, TOL_BF16_FULL_GRAD)])
+def test_config2_untiled_equals_4x4_blocks(name, cfg, tol, gtol):
+    """Statistics and loss to the accumulation-order level; the gradient within the allowance
+    for pooling / ReLU decisions that the two accumulation orders take differently (FP32: 1e-2,
+    BF16: the decision bound)."""
+    a = run_gpu(512, 512, 1, **cfg)
+    b = run_gpu(512, 512, 1, tiles_h=4, tiles_w=4, **cfg)
+    assert a["status"] == 0 and b["status"] == 0
+    for s in range(5):
+        assert rel_l2(b["grams"][s], a["grams"][s]) <= tol, s
+    assert abs(b["E"] - a["E"]) <= tol * abs(a["E"])
+    assert rel_l2(b["g"], a["g"]) <= gtol
+
+
+def test_config2_lbfgs_100_iterations_bf16():
+    from paper_2212_13459_gb300 import synth
+    from tests._gpu import seeded
+    params, u, v, x = seeded(512, 512, 1)
+    ctx = native.Context(synth.flat_params(params), tiles_h=4, tiles_w=4)
+    ctx.style_targets(torch.from_numpy(v).cuda())
+    ctx.content_targets(torch.from_numpy(u).cuda())
+    xt = torch.from_numpy(u.copy()).cuda()
+    losses = []
+    driver.style_transfer(ctx, xt, 100, history=10,
+                          callback=lambda k, l: losses.append(l.item()) if k in (0, 99) else None)
+    assert np.isfinite(losses).all() and losses[1] < 0.5 * losses[0], losses
+    assert ctx.sync_status() == 0
+    ctx.close()

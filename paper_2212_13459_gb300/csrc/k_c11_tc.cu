@@ -83,7 +83,8 @@ constexpr uint32_t kFwdBoxBytes = kFwdBoxH * kFwdBoxW * 16;   // 2,880
 constexpr uint32_t kFwdStage = 3072;                         // box + zeroed tail
 constexpr uint32_t kFwdB = 16384;                            // 5 x 2 KB used, rest zero
 constexpr uint32_t kFwdOut = 128 * 128;                      // one output tile, 128-B swizzle
-constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdStage + 2 * kFwdOut;
+constexpr int kFwdOutBufs = 4;                               // output tiles in flight per CTA
+constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdStage + kFwdOutBufs * kFwdOut;
 
 __device__ __forceinline__ uint64_t desc_k_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
   const uint32_t b_base = smem_base, a_base = smem_base + kFwdB;
-  const uint32_t o_off = kFwdB + kFwdStages * kFwdStage;   // two output staging tiles
+  const uint32_t o_off = kFwdB + kFwdStages * kFwdStage;   // output staging tiles
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = B * tiles_x * tiles_y;
 
@@ -204,8 +205,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     // ---------------- epilogue: bias, ReLU, valid-extent mask, BF16 tile -> TMA store ----------------
     // Each thread writes its pixel's 128-byte row into a 128-byte-swizzled staging tile (chunk c
     // of row r at c ^ (r & 7): conflict-free), and one thread stores the 16 x 8 x 64 tile with
-    // one TMA copy (full-line writes; rows / columns past the buffer are clipped). Two staging
-    // tiles alternate; a tile is rewritten only after its store has finished reading it.
+    // one TMA copy (full-line writes; rows / columns past the buffer are clipped). Four staging
+    // tiles rotate (several stores in flight); a tile is rewritten only after its store has
+    // finished reading it.
     const int q = warp & 3;
     const int row = q * 32 + lane;   // patch pixel (row / 8, row % 8)
     const int et = threadIdx.x - 64;
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
       // one thread waits (bounded) and broadcasts, so all 128 threads leave the loop together;
-      // the same barrier tells everyone that staging tile (it & 1) is free again
+      // the same barrier tells everyone that staging tile it % 4 is free again
       if (et == 0) epi_ok = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1u, &abort_flag, err);
       named_bar_sync(1, 128);
       if (!epi_ok) break;
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       const int y = ty * kFwdTH + row / kFwdTW, x = tx * kFwdTW + row % kFwdTW;
       const BlockGeom g = geom[b];
       const bool valid = y < g.eh && x < g.ew;
-      uint8_t *orow = smem_gen + o_off + (size_t)(it & 1) * kFwdOut + (size_t)row * 128;
+      uint8_t *orow = smem_gen + o_off + (size_t)(it % kFwdOutBufs) * kFwdOut + (size_t)row * 128;
 #pragma unroll
       for (int c = 0; c < 8; c++) {
         const float4 b0 = *reinterpret_cast<const float4 *>(bias_sh + c * 8);
@@ -245,10 +247,10 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       fence_proxy_async_smem();
       named_bar_sync(1, 128);
       if (et == 0) {
-        tma_store_4d(&tmO, smem_base + o_off + (uint32_t)(it & 1) * kFwdOut, 0, tx * kFwdTW,
+        tma_store_4d(&tmO, smem_base + o_off + (uint32_t)(it % kFwdOutBufs) * kFwdOut, 0, tx * kFwdTW,
                      ty * kFwdTH, b);
         bulk_commit();
-        bulk_wait_read_1();
+        bulk_wait_read_3();   // the tile written next (it + 1) was stored at it + 1 - 4
       }
     }
     if (et == 0) bulk_wait_all();

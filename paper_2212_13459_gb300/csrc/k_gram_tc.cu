@@ -128,19 +128,34 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
   }
 }
 
-// Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials
-__global__ void gram_tc_reduce_kernel(const float *__restrict__ part, int nruns, int C, int N,
-                                      int nI, int nJ, double *__restrict__ Gacc) {
+// Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials. A CTA takes 32
+// consecutive elements (one per lane, coalesced reads); its 8 warps split the runs (warp w sums
+// runs w, w + 8, ... in order) and the 8 partial sums are added in warp order (deterministic).
+__global__ void __launch_bounds__(256) gram_tc_reduce_kernel(const float *__restrict__ part,
+                                                             int nruns, int C, int N, int nI,
+                                                             int nJ, double *__restrict__ Gacc) {
+  __shared__ double red[8][32];
   const long long n = (long long)C * C;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / C), j = (int)(e % C);
-    const int tile = (i / 128) * nJ + j / N;
-    const size_t off = ((size_t)tile * 128 + (i % 128)) * N + (j % N);
-    const size_t stride = (size_t)nI * nJ * 128 * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t stride = (size_t)nI * nJ * 128 * N;
+  for (long long e0 = (long long)blockIdx.x * 32; e0 < n; e0 += (long long)gridDim.x * 32) {
+    const long long e = e0 + lane;
     double s = 0.0;
-    for (int r = 0; r < nruns; r++) s += (double)part[(size_t)r * stride + off];
-    Gacc[e] += s;
+    if (e < n) {
+      const int i = (int)(e / C), j = (int)(e % C);
+      const int tile = (i / 128) * nJ + j / N;
+      const size_t off = ((size_t)tile * 128 + (i % 128)) * N + (j % N);
+      for (int r = warp; r < nruns; r += 8) s += (double)part[(size_t)r * stride + off];
+    }
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && e < n) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; w++) t += red[w][lane];
+      Gacc[e] += t;
+    }
+    __syncthreads();
   }
 }
 
@@ -208,7 +223,7 @@ cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStr
   }
   if (e != cudaSuccess) return e;
   const long long n = (long long)a.C * a.C;
-  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+  const int grid = (int)std::min<long long>((n + 31) / 32, 152 * 8);
   gram_tc_reduce_kernel<<<grid, 256, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
   return cudaGetLastError();
 }

@@ -112,6 +112,10 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read_1() {
   asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
 }
+// wait until at most three committed store groups still read their shared-memory sources
+__device__ __forceinline__ void bulk_wait_read_3() {
+  asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+}
 // wait until every committed store group has completed
 __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");

@@ -151,6 +151,13 @@ nst_status nst_set_schedule(nst_ctx *ctx, int schedule);
  * same E and dE/dx up to summation order. Either pointer may be NULL. */
 nst_status nst_pass_info(nst_ctx *ctx, int *batches, int *resident);
 
+/* Check of the failure path (no paper counterpart): one kernel whose bounded mbarrier wait can
+ * never complete (the same wait the convolution kernels use, with a limit of `limit_cycles`
+ * SM cycles, 1 .. 4e9) runs out, latches the timeout in ctx's status word and returns; the next
+ * nst_sync_status then returns NST_ERR_TIMEOUT and clears it, and ctx stays usable. Nothing
+ * faults or hangs. */
+nst_status nst_check_timeout_path(nst_ctx *ctx, long long limit_cycles, void *stream);
+
 /* Synchronize `stream` and return (then clear) the latched device status. */
 nst_status nst_sync_status(nst_ctx *ctx, void *stream);
 

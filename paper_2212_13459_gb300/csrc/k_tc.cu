@@ -811,6 +811,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---- failure path check ----------------------------------------------------------------------------
+// One CTA waits on an mbarrier that nothing will complete, with the same bounded wait the
+// convolution kernels use but a short limit: the wait runs out, kErrTimeout is latched in the
+// status word and the kernel returns. No fault, no hang; the context stays usable.
+__global__ void timeout_check_kernel(long long limit, unsigned *err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_limit(smem_u32(&bar), 0, &abort_flag, err, limit);
+}
+
 // ---- host side -------------------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -1007,6 +1023,11 @@ void *tc_encode_tiled_fn() { return tc_available() ? reinterpret_cast<void *>(g_
 int tc_num_sms() {
   tc_available();
   return g_num_sms;
+}
+
+cudaError_t launch_timeout_check(long long limit_cycles, unsigned *err, cudaStream_t s) {
+  timeout_check_kernel<<<1, 32, 0, s>>>(limit_cycles, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {

@@ -1140,6 +1140,15 @@ nst_status nst_sync_status(nst_ctx *ctx, void *stream) {
   return NST_OK;
 }
 
+nst_status nst_check_timeout_path(nst_ctx *ctx, long long limit_cycles, void *stream) {
+  if (!ctx) return fail(nullptr, NST_ERR_INVALID_ARG, "null context");
+  if (limit_cycles < 1 || limit_cycles > 4000000000LL)
+    return fail(ctx, NST_ERR_INVALID_ARG, "limit out of range");
+  cudaError_t e = launch_timeout_check(limit_cycles, ctx->d_err, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "timeout check launch");
+  return NST_OK;
+}
+
 nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int cout, int taps,
                        const void *in, const void *w, int k2, const void *in2, const void *w2,
                        const float *bias, int mode, const void *mask, const int *geom, void *out,

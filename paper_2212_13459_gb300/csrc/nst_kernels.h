@@ -87,6 +87,8 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s);
 bool tc_available();
 void *tc_encode_tiled_fn();   // cuTensorMapEncodeTiled (driver entry point), null if unavailable
 int tc_num_sms();
+// one bounded mbarrier wait that cannot complete: latches kErrTimeout after limit_cycles
+cudaError_t launch_timeout_check(long long limit_cycles, unsigned *err, cudaStream_t s);
 
 // k_c11_tc.cu: conv1_1 on the tensor cores (BF16 storage). Forward: out[b][y][x][64] =
 // relu(bias + conv1_1(block image)) inside each block's valid extent, zero elsewhere; w11 is

@@ -72,6 +72,7 @@ def lib():
                 "nst_set_timing": ([vp, ip], ip),
                 "nst_sync_status": ([vp, vp], ip),
                 "nst_set_schedule": ([vp, ip], ip),
+                "nst_check_timeout_path": ([vp, ll, vp], ip),
                 "nst_pass_info": ([vp, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int)], ip),
                 "nst_last_error": ([vp], ctypes.c_char_p),
@@ -224,6 +225,10 @@ class Context:
 
     def sync_status(self, stream=None):
         return lib().nst_sync_status(self.h, _stream(stream))
+
+    def check_timeout_path(self, limit_cycles=20_000_000, stream=None):
+        """Run the bounded-wait failure path once (see nst_check_timeout_path)."""
+        _check(lib().nst_check_timeout_path(self.h, int(limit_cycles), _stream(stream)), self.h)
 
     def set_schedule(self, schedule):
         _check(lib().nst_set_schedule(self.h, int(schedule)), self.h)

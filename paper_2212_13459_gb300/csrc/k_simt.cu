@@ -431,6 +431,51 @@ __global__ void unpool_kernel(const T *__restrict__ gp, const T *__restrict__ ac
   }
 }
 
+// Tensor-core form of the same routing: the forward's fused pooling stored 4 bits per pooled
+// value, bit q set where window pixel q (row-major) equals the window max and that max is
+// positive; the gradient goes to the lowest set bit (the first maximum), none where no bit is
+// set (the ReLU gate is shut). One 32-bit word per 8 channels c .. c+7 at byte (p C + c) / 2,
+// channel c+k in the nibble at bit 8 (k & 3) + 4 (k >> 2). The backward reads half a byte per
+// value instead of the four activations.
+__global__ void unpool_idx_kernel(const __nv_bfloat16 *__restrict__ gp,
+                                  const unsigned char *__restrict__ idx,
+                                  __nv_bfloat16 *__restrict__ g, int B, int Hp, int Wp, int C,
+                                  const BlockGeom *__restrict__ geom, int level_out) {
+  const int C8 = C / 8;
+  const long long n = (long long)B * Hp * Wp * C8;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i % C8) * 8;
+    long long p = i / C8;
+    const int x = (int)(p % Wp);
+    const int y = (int)((p / Wp) % Hp);
+    const int b = (int)(p / ((long long)Wp * Hp));
+    const BlockGeom gm = geom[b];
+    const int Wi = 2 * Wp;
+    const size_t o0 = (((size_t)b * 2 * Hp + 2 * y) * Wi + 2 * x) * C + c;
+    const size_t offs[4] = {o0, o0 + C, o0 + (size_t)Wi * C, o0 + (size_t)Wi * C + C};
+    float r[4][8];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int j = 0; j < 8; j++) r[k][j] = 0.f;
+    if (y < (gm.eh >> level_out) && x < (gm.ew >> level_out)) {
+      float gv[8];
+      load8(gp + (size_t)p * C + c, gv);
+      const uint32_t w = *reinterpret_cast<const uint32_t *>(idx + ((size_t)p * C + c) / 2);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const uint32_t nib = (w >> (8 * (j & 3) + 4 * (j >> 2))) & 0xfu;
+        const uint32_t first = nib & (0u - nib);   // lowest set bit, 0 if none
+#pragma unroll
+        for (int q = 0; q < 4; q++) r[q][j] = first == (1u << q) ? gv[j] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) store8(g + offs[k], r[k]);
+  }
+}
+
 static int ew_grid(long long n) {
   long long b = (n + 255) / 256;
   return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
@@ -446,6 +491,12 @@ template <typename T>
 void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C,
                    const BlockGeom *geom, int level_out, cudaStream_t s) {
   unpool_kernel<T><<<ew_grid((long long)B * Hp * Wp * C / 8), 256, 0, s>>>(gp, act, g, B, Hp, Wp,
+                                                                            C, geom, level_out);
+}
+void launch_unpool_idx(const __nv_bfloat16 *gp, const unsigned char *idx, __nv_bfloat16 *g,
+                       int B, int Hp, int Wp, int C, const BlockGeom *geom, int level_out,
+                       cudaStream_t s) {
+  unpool_idx_kernel<<<ew_grid((long long)B * Hp * Wp * C / 8), 256, 0, s>>>(gp, idx, g, B, Hp, Wp,
                                                                             C, geom, level_out);
 }
 template void launch_pool<float>(const float *, float *, int, int, int, int, const BlockGeom *,

@@ -123,6 +123,7 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
       }
     }
   }
+  if (!a.out) return;   // forward with fused pooling and window positions: nothing else reads it
   __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.out) + o;
 #pragma unroll
   for (int q = 0; q < 4; q++) st_bf16x8(out + 8 * q, v + 8 * q);
@@ -134,32 +135,57 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
 // warp at lanes l, l^1, l^TW, l^(TW+1): the max is two shuffles, and the window's top-left lane
 // writes the pooled value (the BF16 values, exactly as stored, so the result equals pooling the
 // stored activation). Outside the block's valid pooled region the pooled map is zero.
+//
+// Window positions for the backward (pool_idx, when a backward pass follows): 4 bits per pooled
+// value, bit q set when window pixel q (row-major: 0 = (y, x), 1 = (y, x+1), 2 = (y+1, x),
+// 3 = (y+1, x+1)) equals the window max and that max is positive. The gradient goes to the lowest
+// set bit, the first maximum, as in routing by the stored activations; no bit = the ReLU gate is
+// shut. Layout: one 32-bit word per 8 channels c .. c+7 at byte (pooled pixel * C + c) / 2, the
+// nibble of channel c+k at bit 8 (k & 3) + 4 (k >> 2).
+__device__ __forceinline__ uint32_t pool_nibble_shift(int k) { return 8 * (k & 3) + 4 * (k >> 2); }
+
 __device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGeom &g, int b,
                                                 int y, int x, int n, int tw, const float *v) {
-  // the stored BF16 values, two channels per register; max over the window with 2 shuffles
-  uint32_t h[16];
+  constexpr int NC = 32, NW = NC / 2;   // channels, BF16 pairs
+  // the stored BF16 values, two channels per register; max over the window with 2 shuffles,
+  // which leave the max in all four lanes of the window
+  uint32_t h[NW], eq[NW];
+  const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
 #pragma unroll
-  for (int j = 0; j < 16; j++) {
-    __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-    h[j] = *reinterpret_cast<uint32_t *>(&p);
-  }
-#pragma unroll
-  for (int j = 0; j < 16; j++) {
-    uint32_t o1 = __shfl_xor_sync(0xffffffffu, h[j], 1);
-    __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162 *>(&h[j]),
-                               *reinterpret_cast<__nv_bfloat162 *>(&o1));
+  for (int j = 0; j < NW; j++) {
+    const __nv_bfloat162 own = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    const uint32_t ou = *reinterpret_cast<const uint32_t *>(&own);
+    uint32_t o1 = __shfl_xor_sync(0xffffffffu, ou, 1);
+    __nv_bfloat162 m = __hmax2(own, *reinterpret_cast<__nv_bfloat162 *>(&o1));
     uint32_t mu = *reinterpret_cast<uint32_t *>(&m);
     uint32_t o2 = __shfl_xor_sync(0xffffffffu, mu, tw);
     m = __hmax2(m, *reinterpret_cast<__nv_bfloat162 *>(&o2));
     h[j] = *reinterpret_cast<uint32_t *>(&m);
+    if (a.pool_idx) eq[j] = __heq2_mask(own, m) & __hgt2_mask(m, zero2);   // 0xffff: flagged
+  }
+  uint32_t idx[NC / 8];
+  if (a.pool_idx) {
+    const uint32_t qbit = 0x11111111u << ((x & 1) | ((y & 1) << 1));
+#pragma unroll
+    for (int i = 0; i < NC / 8; i++) {
+      const uint32_t lo = __byte_perm(eq[4 * i], eq[4 * i + 1], 0x6420);      // channels 0..3
+      const uint32_t hi = __byte_perm(eq[4 * i + 2], eq[4 * i + 3], 0x6420);  // channels 4..7
+      uint32_t w = ((lo & 0x0f0f0f0fu) | (hi & 0xf0f0f0f0u)) & qbit;
+      w |= __shfl_xor_sync(0xffffffffu, w, 1);
+      w |= __shfl_xor_sync(0xffffffffu, w, tw);
+      idx[i] = w;
+    }
   }
   if ((y & 1) || (x & 1) || y >= a.Hb || x >= a.Wb) return;
   const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
   const bool valid = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
-  uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) +
-                                         (((size_t)b * Hp + py) * Wp + px) * a.cout + n);
+  const size_t po = (((size_t)b * Hp + py) * Wp + px) * a.cout + n;
+  if (a.pool_idx)
+    *reinterpret_cast<uint4 *>(a.pool_idx + po / 2) =
+        valid ? make_uint4(idx[0], idx[1], idx[2], idx[3]) : make_uint4(0u, 0u, 0u, 0u);
+  uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + po);
 #pragma unroll
-  for (int q = 0; q < 4; q++)
+  for (int q = 0; q < NC / 8; q++)
     out[q] = valid ? make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3])
                    : make_uint4(0u, 0u, 0u, 0u);
 }
@@ -218,7 +244,7 @@ __device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g,
       for (int j = 0; j < 8; j++) v[j] = m8[j] > 0.f ? v[j] : 0.f;
     }
   }
-  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.out) + o, v);
+  if (a.out) st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.out) + o, v);
 }
 
 // fused 2 x 2 max pool of a 32-pixel chunk (whole rows of a patch 8 or 16 wide) from the warp's
@@ -239,6 +265,7 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
   const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
   const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
   float m[8];
+  int k8[8];   // window position (row-major) of the first maximum
 #pragma unroll
   for (int qq = 0; qq < 4; qq++) {
     // odd windows visit their pixels in the order 1, 0, 3, 2: the two windows of a quarter-warp
@@ -252,7 +279,10 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
     for (int i = 0; i < 8; i++) {
       const float s = __bfloat162float(__float2bfloat16_rn(valid ? fmaxf(r[i] + bb[i], 0.f)
                                                                  : 0.f));
-      m[i] = qq == 0 ? s : fmaxf(m[i], s);
+      if (qq == 0 || s > m[i] || (s == m[i] && q < k8[i])) {
+        m[i] = s;
+        k8[i] = q;
+      }
     }
   }
   const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
@@ -261,9 +291,15 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
 #pragma unroll
     for (int i = 0; i < 8; i++) m[i] = 0.f;
   }
-  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + (((size_t)b * Hp + py) * Wp + px) *
-                                                                 a.cout + n + cg * 8,
-            m);
+  const size_t po = (((size_t)b * Hp + py) * Wp + px) * a.cout + n + cg * 8;
+  st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + po, m);
+  if (a.pool_idx) {   // window positions, in the format of pool_epilogue32 (first max only)
+    uint32_t w = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      if (m[i] > 0.f) w |= (1u << k8[i]) << pool_nibble_shift(i);
+    *reinterpret_cast<uint32_t *>(a.pool_idx + po / 2) = w;
+  }
 }
 
 // ---- the kernel -------------------------------------------------------------------------------------

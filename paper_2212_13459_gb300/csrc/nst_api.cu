@@ -256,14 +256,22 @@ float bf2f(uint16_t h) {
 }
 
 // ---- pass plan --------------------------------------------------------------------------------------
-size_t tile_bytes(int Hb, int Wb, size_t esz) {
+// Bytes of the per-layer buffer of conv l: its activation, or, for a layer followed by pooling in
+// the tensor-core form, the window positions of the fused pooling (4 bits per pooled value; the
+// full-resolution activation is then never stored).
+size_t layer_bytes(int l, size_t px, size_t esz, bool pool_positions) {
+  if (pool_positions && kPoolAfter[l]) return (px >> (2 * (kLevel[l] + 1))) * kCout[l] / 2;
+  return (px >> (2 * kLevel[l])) * kCout[l] * esz;
+}
+
+size_t tile_bytes(int Hb, int Wb, size_t esz, bool pool_positions) {
   size_t px = (size_t)Hb * Wb, tot = 0;
   for (int l = 0; l < kNConv; l++) {
-    tot += (px >> (2 * kLevel[l])) * kCout[l];
-    if (kPoolAfter[l]) tot += (px >> (2 * (kLevel[l] + 1))) * kCout[l];
+    tot += layer_bytes(l, px, esz, pool_positions);
+    if (kPoolAfter[l]) tot += (px >> (2 * (kLevel[l] + 1))) * kCout[l] * esz;
   }
-  tot += 2 * px * 64;  // two gradient buffers
-  return tot * esz;
+  tot += 2 * px * 64 * esz;  // two gradient buffers
+  return tot;
 }
 
 nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
@@ -281,7 +289,7 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
   p.Wb = (mw + 15) / 16 * 16;
   long long limit = ctx->cfg.workspace_limit_bytes > 0 ? ctx->cfg.workspace_limit_bytes
                                                        : kDefaultWorkspace;
-  long long per = (long long)tile_bytes(p.Hb, p.Wb, ctx->esz);
+  long long per = (long long)tile_bytes(p.Hb, p.Wb, ctx->esz, ctx->use_tc);
   int B = (int)std::max(1LL, limit / std::max(per, 1LL));
   if (ctx->cfg.max_batch_tiles > 0) B = std::min(B, ctx->cfg.max_batch_tiles);
   B = std::min(B, nt);
@@ -400,7 +408,7 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
 }
 
 nst_status ensure_buffers(nst_ctx *ctx, const PassPlan &p, Workspace &ws) {
-  const size_t per = tile_bytes(p.Hb, p.Wb, ctx->esz);
+  const size_t per = tile_bytes(p.Hb, p.Wb, ctx->esz, ctx->use_tc);
   const size_t need = per * p.Bmax + 64 * 256;
   if (need > ctx->ws_cap) {
     if (ctx->d_ws) CK(cudaFree(ctx->d_ws));
@@ -413,7 +421,7 @@ nst_status ensure_buffers(nst_ctx *ctx, const PassPlan &p, Workspace &ws) {
   const size_t px = (size_t)p.Bmax * p.Hb * p.Wb;
   for (int l = 0; l < kNConv; l++) {
     ws.act[l] = q;
-    q += align256((px >> (2 * kLevel[l])) * kCout[l] * ctx->esz);
+    q += align256(layer_bytes(l, px, ctx->esz, ctx->use_tc));
     ws.pool[l] = nullptr;
     if (kPoolAfter[l]) {
       ws.pool[l] = q;
@@ -465,7 +473,7 @@ nst_status run_conv(nst_ctx *ctx, ConvArgs a, cudaStream_t s) {
 
 template <typename T>
 nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const Workspace &ws,
-                         const float *img, int last_conv, cudaStream_t s) {
+                         const float *img, int last_conv, bool for_backward, cudaStream_t s) {
   const BlockGeom *geom = p.d_geom + bt.t0;
   {
     Timer tm(ctx, kTOther, s);
@@ -492,9 +500,15 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
     a.bias = ctx->d_bias[l];
     a.geom = geom;
     a.level = lv;
-    // the tensor-core epilogue writes the pooled map too
-    const bool fuse_pool = ctx->use_tc && kPoolAfter[l] && l < last_conv;
-    if (fuse_pool) a.pool_out = ws.pool[l];
+    // the tensor-core epilogue writes the pooled map and, when a backward pass follows, the
+    // window position of each pooled value (the backward's routing) in place of the activation
+    const bool fuse_pool = ctx->use_tc && kPoolAfter[l];
+    if (fuse_pool) {
+      if (l >= last_conv) return fail(ctx, NST_ERR_STATE, "pass ends at a pooled layer");
+      a.pool_out = ws.pool[l];
+      a.out = nullptr;
+      a.pool_idx = for_backward ? (unsigned char *)ws.act[l] : nullptr;
+    }
     nst_status st = run_conv(ctx, a, s);
     if (st) return st;
     if (kPoolAfter[l] && l < last_conv && !fuse_pool) {
@@ -634,8 +648,13 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
     if (kPoolAfter[lp]) {
       Timer tm(ctx, kTOther, s);
       ctx->launches++;
-      launch_unpool<T>((const T *)ws.g[1 - cur], (const T *)ws.act[lp], (T *)ws.g[cur], bt.B,
-                       p.Hb >> lv, p.Wb >> lv, kCout[lp], geom, lv, s);
+      if (ctx->use_tc)
+        launch_unpool_idx((const __nv_bfloat16 *)ws.g[1 - cur], (const unsigned char *)ws.act[lp],
+                          (__nv_bfloat16 *)ws.g[cur], bt.B, p.Hb >> lv, p.Wb >> lv, kCout[lp],
+                          geom, lv, s);
+      else
+        launch_unpool<T>((const T *)ws.g[1 - cur], (const T *)ws.act[lp], (T *)ws.g[cur], bt.B,
+                         p.Hb >> lv, p.Wb >> lv, kCout[lp], geom, lv, s);
     } else {
       cur = 1 - cur;
     }
@@ -671,7 +690,7 @@ nst_status stats_pass(nst_ctx *ctx, const float *img, int H, int W, PassKind kin
   const int nt = (int)p->tiles.size();
   for (const Batch &bt : p->batches) {
     const int last = kind == kPassContentTarget ? kContentConv : kNConv - 1;
-    st = forward_batch<T>(ctx, *p, bt, ws, img, last, s);
+    st = forward_batch<T>(ctx, *p, bt, ws, img, last, false, s);
     if (st) return st;
     if (kind == kPassStyleStats) {
       st = gram_batch<T>(ctx, *p, bt, ws, s, moments);
@@ -711,7 +730,7 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   ctx->pass_batches = (int)p->batches.size();
   if (resident) {
     const Batch &bt = p->batches[0];
-    st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, s);
+    st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, true, s);
     if (st) return st;
     st = gram_batch<T>(ctx, *p, bt, ws, s, ctx->aug);
     if (st) return st;
@@ -752,7 +771,7 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   const int nt = (int)p->tiles.size();
   for (const Batch &bt : p->batches) {
     if (!resident) {
-      st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, s);
+      st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, true, s);
       if (st) return st;
     }
     {

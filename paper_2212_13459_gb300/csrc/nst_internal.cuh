@@ -78,6 +78,8 @@ struct ConvArgs {
                           // [B][Hb/2][Wb/2][cout] (null = no fused pooling)
   const float *addvec;    // backward: per-channel term added at valid pixels before the gate
                           // (alpha of the mean / std loss, Table 1 rows 3-4), or null
+  unsigned char *pool_idx;  // forward with pool_out: also the window positions of the maximum,
+                            // 4 bits per pooled value ([B][Hb/2][Wb/2][cout] / 2 bytes), or null
 };
 
 }  // namespace nst

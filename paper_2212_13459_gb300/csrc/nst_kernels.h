@@ -58,6 +58,10 @@ void launch_pool(const T *in, T *out, int B, int Hp, int Wp, int C, const BlockG
 template <typename T>
 void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C,
                    const BlockGeom *geom, int level_out, cudaStream_t s);
+// tensor-core form: routing by the window positions the fused forward pooling stored
+void launch_unpool_idx(const __nv_bfloat16 *gp, const unsigned char *idx, __nv_bfloat16 *g,
+                       int B, int Hp, int Wp, int C, const BlockGeom *geom, int level_out,
+                       cudaStream_t s);
 template <typename T>
 void launch_gram_partial(const T *V, int Hb, int Wb, int C, const OwnRect *own,
                          const GramChunk *chunks, int nchunks, float *part, cudaStream_t s);

@@ -498,9 +498,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const TcGeom tg) {
   using Cfg = HaloCfg<BN, KB, P2KB, NT>;
   constexpr int STAGES = Cfg::STAGES;
-  // accumulators in TMEM: four for the 64-wide slices (their tiles are short, so more tiles in
-  // flight keep the tensor pipe fed while the epilogue drains), two otherwise
-  constexpr int NACC = BN == 64 ? 4 : 2;
+  // four accumulators in TMEM (512 columns at N = 128): the tiles are short, and more tiles in
+  // flight keep the tensor pipe fed while the epilogue drains
+  constexpr int NACC = 4;
   constexpr uint32_t TMEM_COLS = NACC * BN;
   constexpr uint32_t IDESC = make_idesc(BN);
   constexpr int KBT = KB + P2KB;   // K-blocks per tile
@@ -572,56 +572,62 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      bool ok = mbar_wait(smem_u32(&w_bar), 0, &abort_flag, a.err);
-      int stage = 0;
-      uint32_t phase = 0;
-      int it = 0;
-      for (int t = m_first; t < m_total && ok; t += m_step, it++) {
-        const int acc = it % NACC;
-        const uint32_t use = (uint32_t)(it / NACC);
-        if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
+    // The whole warp runs the issue loop, so its descriptor arithmetic is warp-uniform, and one
+    // elected lane issues each MMA and commit: a loop run by a single lane issues several times
+    // slower once epilogue warps keep this warp's scheduler busy, and a 64-wide MMA takes only
+    // 48 cycles. (The 256-wide MMAs of the other kernels take 128 cycles; there the single-lane
+    // loop keeps up and measured slightly faster.)
+    bool ok = mbar_wait_warp(smem_u32(&w_bar), 0, &abort_flag, a.err);
+    int stage = 0;
+    uint32_t phase = 0;
+    int it = 0;
+    for (int t = m_first; t < m_total && ok; t += m_step, it++) {
+      const int acc = it % NACC;
+      const uint32_t use = (uint32_t)(it / NACC);
+      if (!mbar_wait_warp(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
+      tc_fence_after();
+      const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+      bool first = true;
+      for (int kb = 0; kb < KBT; kb++) {
+        if (!mbar_wait_warp(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(acc * BN);
-        bool first = true;
-        for (int kb = 0; kb < KBT; kb++) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = a_base + stage * kHaloStage;
-          // shifted by whole 128-byte rows; the swizzle follows absolute address bits, so the
-          // phase field stays 0 (the box itself starts 1024-aligned). Descriptors are the stage's
-          // base descriptors plus compile-time offsets (address field in 16-byte units).
-          const uint64_t da0 = sw128_desc_k(sa, kHaloBoxW * 128, 0);
-          if (kb < KB) {
-            const uint64_t db0 = sw128_desc(w_base + kb * Cfg::TILE_B);
+        const uint32_t sa = a_base + stage * kHaloStage;
+        // shifted by whole 128-byte rows; the swizzle follows absolute address bits, so the
+        // phase field stays 0 (the box itself starts 1024-aligned). Descriptors are the stage's
+        // base descriptors plus compile-time offsets (address field in 16-byte units).
+        const uint64_t da0 = sw128_desc_k(sa, kHaloBoxW * 128, 0);
+        if (kb < KB) {
+          const uint64_t db0 = sw128_desc(w_base + kb * Cfg::TILE_B);
 #pragma unroll
-            for (int tap = 0; tap < 9; tap++) {
-              const uint64_t da = da0 + (uint64_t)(((tap / 3) * kHaloBoxW + tap % 3) * 8);
-              const uint64_t db = db0 + (uint64_t)(tap * KB * (Cfg::TILE_B >> 4));
-#pragma unroll
-              for (int k = 0; k < kBK / 16; k++) {
-                mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
-                         first ? 0u : 1u);
-                first = false;
-              }
-            }
-          } else {   // phase 2: the V R term, centre tap only
-            const uint64_t da = da0 + (uint64_t)((kHaloBoxW + 1) * 8);
-            const uint64_t db = sw128_desc(w_base + (9 * KB + kb - KB) * Cfg::TILE_B);
+          for (int tap = 0; tap < 9; tap++) {
+            const uint64_t da = da0 + (uint64_t)(((tap / 3) * kHaloBoxW + tap % 3) * 8);
+            const uint64_t db = db0 + (uint64_t)(tap * KB * (Cfg::TILE_B >> 4));
 #pragma unroll
             for (int k = 0; k < kBK / 16; k++) {
-              mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, first ? 0u : 1u);
+              if (elect_one())
+                mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
+                         first ? 0u : 1u);
               first = false;
             }
           }
-          mma_commit(smem_u32(&empty_bar[stage]));
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        } else {   // phase 2: the V R term, centre tap only
+          const uint64_t da = da0 + (uint64_t)((kHaloBoxW + 1) * 8);
+          const uint64_t db = sw128_desc(w_base + (9 * KB + kb - KB) * Cfg::TILE_B);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; k++) {
+            if (elect_one())
+              mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, first ? 0u : 1u);
+            first = false;
+          }
         }
-        if (ok) mma_commit(smem_u32(&tfull_bar[acc]));
+        if (elect_one()) mma_commit(smem_u32(&empty_bar[stage]));
+        if (++stage == STAGES) { stage = 0; phase ^= 1; }
       }
+      if (!ok) break;
+      if (elect_one()) mma_commit(smem_u32(&tfull_bar[acc]));
     }
   } else {
     const int q = warp & 3;

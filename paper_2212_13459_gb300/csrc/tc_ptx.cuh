@@ -86,6 +86,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
                                           unsigned *err) {
   return mbar_wait_limit(bar, parity, abort_flag, err, kWaitCycles);
 }
+// Bounded wait taken by lane 0 and broadcast, so that the whole warp continues or leaves as one.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity,
+                                               volatile int *abort_flag, unsigned *err) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+// One lane of a fully active warp (the same lane every time): the issuing lane of tcgen05.mma
+// and tcgen05.commit in loops that the whole warp runs.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p = 0;
+  asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\tselp.u32 %0, 1, 0, e;\n\t}\n"
+               : "=r"(p));
+  return p != 0;
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int c0, int c1, int c2, int c3) {
   asm volatile(

@@ -72,8 +72,12 @@ __device__ __forceinline__ void st_bf16x8(__nv_bfloat16 *p, const float *v) {
   *reinterpret_cast<uint4 *>(p) = t;
 }
 
+// mrow: when non-null, the ReLU mask of this pixel is read from shared memory instead of a.mask:
+// the pixel's 128-byte row (64 channels) of a TMA box with the 128-byte swizzle, whose 16-byte
+// chunk j sits at chunk j ^ mswz (mswz = the row's index within its 1024-byte group).
 __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g, int b, int y,
-                                           int x, int n, float *v) {
+                                           int x, int n, float *v, const uint8_t *mrow = nullptr,
+                                           int mswz = 0) {
   const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
   const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
   if (a.mode == kEpiForward) {
@@ -111,7 +115,20 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
 #pragma unroll
         for (int j = 0; j < 32; j++) v[j] += __ldg(a.addvec + n + j);
       }
-      if (a.mask) {
+      if (mrow) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const uint4 raw = *reinterpret_cast<const uint4 *>(
+              mrow + ((((n & 63) / 8 + q) ^ mswz) << 4));
+          const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+          for (int i = 0; i < 4; i++) {
+            const float2 f = __bfloat1622float2(h[i]);
+            v[8 * q + 2 * i] = f.x > 0.f ? v[8 * q + 2 * i] : 0.f;
+            v[8 * q + 2 * i + 1] = f.y > 0.f ? v[8 * q + 2 * i + 1] : 0.f;
+          }
+        }
+      } else if (a.mask) {
         const __nv_bfloat16 *mk = reinterpret_cast<const __nv_bfloat16 *>(a.mask) + o;
 #pragma unroll
         for (int q = 0; q < 4; q++) {
@@ -489,7 +506,7 @@ struct HaloCfg {
   static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloStage;
 };
 
-template <int BN, int KB, int P2KB, int NT>
+template <int BN, int KB, int P2KB, int NT, bool MASK_SMEM>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB,
@@ -504,6 +521,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t TMEM_COLS = NACC * BN;
   constexpr uint32_t IDESC = make_idesc(BN);
   constexpr int KBT = KB + P2KB;   // K-blocks per tile
+  // MASK_SMEM: the phase-2 K-block is the fused V R term of an input gradient whose ReLU mask
+  // is that same activation V; the epilogue reads the mask from the K-block's box, which covers
+  // the tile plus a one-pixel border, and the box's stage is released by the epilogue warps,
+  // not by the MMA. Each tile's phase-2 box lands in an odd stage.
+  static_assert(!MASK_SMEM || (KB == 1 && P2KB == 1 && STAGES % 2 == 0 && NT == 1 && BN == 64),
+                "mask from the phase-2 box");
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], w_bar;
@@ -521,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), MASK_SMEM && (s & 1) ? kEpiThreads / 32 : 1);
     }
     mbar_init(smem_u32(&w_bar), 1);
     for (int i = 0; i < NACC; i++) {
@@ -623,7 +646,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             first = false;
           }
         }
-        if (elect_one()) mma_commit(smem_u32(&empty_bar[stage]));
+        if (!(MASK_SMEM && kb == KB)) {   // (that box is released by the epilogue)
+          if (elect_one()) mma_commit(smem_u32(&empty_bar[stage]));
+        }
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       }
       if (!ok) break;
@@ -649,11 +674,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool inb = y < a.Hb && x < a.Wb;
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+      // the ReLU mask from the tile's phase-2 box (this pixel's row: box pixel (y + 1, x + 1));
+      // its full barrier completed before the MMAs that the accumulator waited for, and waiting
+      // on it here acquires the TMA's writes
+      const uint8_t *mrow = nullptr;
+      int mswz = 0, ms = 0;
+      if constexpr (MASK_SMEM) {
+        const int gk = it * KBT + KB;
+        ms = gk % STAGES;
+        int mok = 0;
+        if (lane == 0)
+          mok = mbar_wait_sleep(smem_u32(&full_bar[ms]), (uint32_t)(gk / STAGES) & 1u,
+                                &abort_flag, a.err);
+        if (!__shfl_sync(0xffffffffu, mok, 0)) break;
+        const int pbox = (row / kHaloTW + 1) * kHaloBoxW + row % kHaloTW + 1;
+        mrow = smem_raw + (a_base - smem_u32(smem_raw)) + (size_t)ms * kHaloStage +
+               (size_t)pbox * 128;
+        mswz = pbox & 7;
+      }
 #pragma unroll 1
       for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
         float v[32];
         tmem_ld32(tbase + (uint32_t)c, v);
-        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v);
+        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v, mrow, mswz);
         if (a.pool_out) {
           if (!inb) {
 #pragma unroll
@@ -664,6 +707,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
+      if constexpr (MASK_SMEM) {   // every lane has read its mask row: release the box's stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty_bar[ms]));
+      }
     }
   }
   tc_fence_before();
@@ -981,7 +1028,7 @@ void pick_patch_rows(int H, int W, int rows, int &TH, int &TW, bool pool) {
   }
 }
 
-template <int BN, int KB, int P2KB, int NT>
+template <int BN, int KB, int P2KB, int NT, bool MASK_SMEM = false>
 cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, cudaStream_t s) {
   using Cfg = HaloCfg<BN, KB, P2KB, NT>;
@@ -989,7 +1036,7 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   static_assert(Cfg::SMEM <= kHaloSmemMax, "halo kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2KB, NT>,
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2KB, NT, MASK_SMEM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
@@ -1004,7 +1051,8 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   tg.total = a.B * tg.tiles_x * tg.tiles_y;   // M tiles; every slice covers all of them
   int grid = std::min(tg.total * NT, g_num_sms);
   grid = std::max(NT, grid / NT * NT);
-  conv_tc_halo_kernel<BN, KB, P2KB, NT><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2, a, tg);
+  conv_tc_halo_kernel<BN, KB, P2KB, NT, MASK_SMEM><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2,
+                                                                                  a, tg);
   return cudaGetLastError();
 }
 
@@ -1049,7 +1097,12 @@ cudaError_t launch_conv_tc_halo(const ConvArgs &a, int BN, int KB, int P2KB, int
     mB2 = mB;
   }
   if (BN == 64 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<64, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
-  if (BN == 64 && KB == 1 && P2KB == 1 && NT == 1) return launch_halo<64, 1, 1, 1>(mA, mB, mA2, mB2, a, s);
+  if (BN == 64 && KB == 1 && P2KB == 1 && NT == 1) {
+    // the ReLU mask of an input gradient is usually the V of its fused V R term: read it from
+    // the phase-2 box then
+    if (a.mask == a.A2 && a.k2 == a.cout) return launch_halo<64, 1, 1, 1, true>(mA, mB, mA2, mB2, a, s);
+    return launch_halo<64, 1, 1, 1>(mA, mB, mA2, mB2, a, s);
+  }
   if (BN == 128 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<128, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
   if (BN == 64 && KB == 2 && P2KB == 0 && NT == 1) return launch_halo<64, 2, 0, 1>(mA, mB, mA2, mB2, a, s);
   return cudaErrorInvalidValue;

@@ -89,6 +89,34 @@ def test_single_layer_bf16(engine, case):
         assert torch.count_nonzero(out[b, :, geom[b, 3]:]).item() == 0
 
 
+@pytest.mark.parametrize("B,H,W", [(1, 64, 64), (2, 37, 29), (3, 16, 8)])
+def test_single_layer_mask_is_phase2_activation(B, H, W):
+    """The input gradient of conv1_2: 64 -> 64 channels, the fused V R term's V is also the ReLU
+    mask (the same tensor), so the tensor-core kernel reads the mask from the V box it already
+    holds in shared memory and releases that box from its epilogue. V is a ReLU output (about
+    half zeros) so that the mask gates; ragged sizes leave partial tiles and invalid rows."""
+    g = torch.Generator(device="cuda").manual_seed(B * 100 + H + W)
+    bf = torch.bfloat16
+    inp = torch.randn(B, H, W, 64, device="cuda", generator=g).to(bf)
+    w = (torch.randn(64, 9, 64, device="cuda", generator=g) / 24.0).to(bf)
+    v = torch.relu(torch.randn(B, H, W, 64, device="cuda", generator=g)).to(bf)
+    w2 = (torch.randn(64, 64, device="cuda", generator=g) / 8.0).to(bf)
+    bias = torch.zeros(64, device="cuda")
+    geom = torch.tensor([[0, 0, H - (b % 2) * 2, W - (b % 2) * 3] for b in range(B)],
+                        dtype=torch.int32, device="cuda")
+    out = torch.full((B, H, W, 64), 7.0, device="cuda", dtype=bf)
+    native.conv3x3(native.PREC_BF16, native.CONV_TC, inp, w, out, bias=bias, mode=1, mask=v,
+                   in2=v, w2=w2, geom=geom, taps=9)
+    torch.cuda.synchronize()
+    ref = _ref(inp, w, v, w2, bias, 1, v, geom.cpu())
+    assert (v.float() == 0).float().mean().item() > 0.3
+    err = (out.float() - ref).norm() / ref.norm()
+    assert err.item() <= 1e-2, err.item()
+    for b in range(B):
+        assert torch.count_nonzero(out[b, geom[b, 2]:]).item() == 0
+        assert torch.count_nonzero(out[b, :, geom[b, 3]:]).item() == 0
+
+
 def test_single_layer_fp32_simt():
     B, H, W, cin, cout = 2, 10, 23, 64, 128
     g = torch.Generator(device="cuda").manual_seed(5)

@@ -37,6 +37,11 @@ METRIC = "megapixels/s of loss+image-gradient evals at 3024×4032; % BF16 TC pea
 # algorithmic FLOPs per image pixel of one evaluation: 2 VGG-19 forwards to ReLU5_1, one
 # input-gradient pass, Gram accumulation and style-gradient products (2 * 34,816)
 FLOP_PER_PX = 2 * 722304 + 722304 + 2 * 34816
+# the part of that work done by the tcgen05 convolution launches: the forward of conv1_2 ..
+# conv5_1 twice (Step 1 and Step 2), their input gradients, and the style-gradient products V R
+# fused into the input-gradient launches (conv1_1, 3,456 FLOP/px each way, and the Gram products
+# run in other kernels)
+CONV_FLOP_PER_PX = 3 * (722304 - 3456) + 34816
 
 WORKLOADS = {
     "scale3": dict(H=3024, W=4032, Hv=2113, Wv=2660, seed=3, tiles=8, small=(1512, 2016)),
@@ -355,14 +360,21 @@ def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E
     peak_conv = peaks["bf16_sus"] if prec == native.PREC_BF16 else None
     roofline = None
     if prec == native.PREC_BF16 and conv_tflops:
-        roofline = {"bound": "tensor", "kernel": "conv_tc_kernel (tcgen05 implicit-GEMM conv)",
-                    "achieved": conv_tflops, "peak": peak_conv, "unit": "TFLOP/s",
-                    "frac": conv_tflops / peak_conv,
-                    "traffic": read_traffic(tm["conv_flops"] / max(1, tm["conv_launches"])),
+        launches = max(1, tm["conv_launches"])
+        alg_per_launch = CONV_FLOP_PER_PX * H * W * args.steps / launches
+        alg_tflops = alg_per_launch / (tm["conv_ms"] / launches / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "tcgen05 convolutions (conv_tc_kernel, "
+                                                 "conv_tc_swap_kernel, conv_tc_halo_kernel)",
+                    "achieved": alg_tflops, "peak": peak_conv, "unit": "TFLOP/s",
+                    "frac": alg_tflops / peak_conv, "frac_algorithmic": alg_tflops / peak_conv,
+                    "traffic": read_traffic(tm["conv_flops"] / launches),
                     "peak_source": "%s bf16_tflops_sustained" % peaks["source"],
+                    "algorithmic_flops_per_launch": alg_per_launch,
+                    "achieved_executed": conv_tflops, "frac_executed": conv_tflops / peak_conv,
+                    "executed_flops_per_launch": tm["conv_flops"] / launches,
+                    "executed_over_algorithmic": tm["conv_flops"] / launches / alg_per_launch,
                     "launches_per_step": tm["conv_launches"] / args.steps,
-                    "ms_per_step": tm["conv_ms"] / args.steps,
-                    "flops_per_launch": tm["conv_flops"] / max(1, tm["conv_launches"])}
+                    "ms_per_step": tm["conv_ms"] / args.steps}
     alg_tflops = FLOP_PER_PX * H * W / (ms_step / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
@@ -397,7 +409,9 @@ def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E
     }
     ctx.close()
     if args.compare_fp32 and prec == native.PREC_BF16:
-        out["fp32_form"] = fp32_compare(flat, u, v, x, grad, k, args, dev)
+        out["fp32_form"] = fp32_compare(flat, u, v, x, grad, k, args, dev, ms_step)
+    if args.workload == "scale3" and prec == native.PREC_BF16 and not args.no_scale4:
+        out["scale4"] = scale4_leg(args, dev)
     if not args.no_cpu_baseline:
         rate, dt, n, threads = cpu_oracle_rate(seed)
         out["cpu_baseline"] = {"value": rate, "unit": "Mpx/s", "cores": threads, "kind": "oracle",
@@ -408,7 +422,7 @@ def report(args, ctx, tm, prec, ms_step, value, world, wl, H, W, seed, k, clk, E
     print(json.dumps(out), flush=True)
 
 
-def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev):
+def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev, bf16_ms):
     """The plain FP32 form (CUDA-core convolutions, FP32 storage) on the same GPU: time and the
     BF16 gradient's relative error against it."""
     import torch
@@ -433,7 +447,67 @@ def fp32_compare(flat, u, v, x, grad_bf16, k, args, dev):
     ctx.close()
     H, W = x.shape[1], x.shape[2]
     return {"ms_per_step": ms, "value": H * W / ms / 1e3, "unit": "Mpx/s",
-            "bf16_speedup": None, "bf16_grad_rel_err_vs_fp32": rel, "loss_fp32": loss.item()}
+            "bf16_speedup": ms / bf16_ms, "bf16_grad_rel_err_vs_fp32": rel,
+            "loss_fp32": loss.item()}
+
+
+def scale4_leg(args, dev, steps=2):
+    """The scale-4 configuration on the same GPU: content 6048 x 8064 (x0 = bicubic x2 of a
+    synthetic 3024 x 4032 previous-scale result), style 4226 x 5319 stroke texture, 16 x 16
+    blocks, BF16. Device time of `steps` evaluations with the printed two-pass schedule and with
+    the resident one, and the device memory in use."""
+    import torch
+    from paper_2212_13459_gb300 import native, synth
+    wl = WORKLOADS["scale4"]
+    H, W, seed, k = wl["H"], wl["W"], wl["seed"], wl["tiles"]
+    t0 = time.perf_counter()
+    flat = synth.flat_params(synth.vgg19_params(seed))
+    v = torch.from_numpy(synth.stroke_style(wl["Hv"], wl["Wv"], seed)).to(dev)
+    u = torch.from_numpy(synth.content_image(H, W, seed)).to(dev)
+    xs = torch.from_numpy(synth.scale2_result(wl["small"][0], wl["small"][1], seed)).to(dev)
+    x = torch.empty((3, H, W), device=dev)
+    native.upsample_init(xs, x)
+    del xs
+    host_s = time.perf_counter() - t0
+    ctx = native.Context(flat, tiles_h=k, tiles_w=k, precision=native.PREC_BF16,
+                         margin1=args.margin1, margin2=args.margin2,
+                         workspace_limit_bytes=int(args.workspace_gb * 1e9),
+                         schedule=native.SCHED_TWO_PASS)
+    ctx.style_targets(v)
+    ctx.content_targets(u)
+    del u, v
+    grad = torch.empty_like(x)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    res = {"workload": "content %dx%d (x0 = bicubic x2 of a synthetic %dx%d previous-scale "
+                       "result), style %dx%d stroke texture, seed %d, %dx%d blocks, margins "
+                       "%d/%d, BF16" % (H, W, wl["small"][0], wl["small"][1], wl["Hv"], wl["Wv"],
+                                        seed, k, k, args.margin1, args.margin2),
+           "steps": steps, "input_generation_s": host_s}
+    stream = torch.cuda.current_stream(dev)
+    for sched, name in ((native.SCHED_TWO_PASS, "two_pass"), (native.SCHED_AUTO, "resident")):
+        ctx.set_schedule(sched)
+        ctx.loss_grad(x, grad, loss)
+        torch.cuda.synchronize(dev)
+        if ctx.sync_status() != 0:
+            raise RuntimeError("scale-4 device status: %s" % native.lib().nst_last_error(ctx.h))
+        torch.cuda.empty_cache()
+        free_b, total_b = torch.cuda.mem_get_info(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.loss_grad(x, grad, loss)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        batches, resident = ctx.pass_info()
+        res[name] = {"value": H * W / ms / 1e3, "unit": "Mpx/s", "ms_per_step": ms,
+                     "hbm_used_gb": (total_b - free_b) / 1e9, "step2_batches": batches,
+                     "resident": resident, "loss": float(loss.item()),
+                     "algorithmic_tflops": FLOP_PER_PX * H * W / (ms / 1e3) / 1e12}
+    ctx.close()
+    del x, grad
+    torch.cuda.empty_cache()
+    return res
 
 
 def read_traffic(flops_per_launch):
@@ -475,6 +549,8 @@ def main():
     ap.add_argument("--no-driver", action="store_true", help="skip the L-BFGS step timing")
     ap.add_argument("--no-resident", action="store_true",
                     help="skip the resident-schedule leg")
+    ap.add_argument("--no-scale4", action="store_true",
+                    help="skip the 6048 x 8064 scale-4 leg of the default workload")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

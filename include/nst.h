@@ -131,7 +131,8 @@ nst_status nst_get_style_moments(nst_ctx *ctx, double *mean_host, double *std_ho
 
 /* Per-kernel-class device time accumulated since the last nst_set_timing() call (CUDA events
  * around every launch while timing is enabled), in milliseconds, and the FLOPs the convolution
- * launches executed (2 * pixels * Cout * (9 Cin + K2) per launch, padding included):
+ * launches executed (2 * pixels * Cout * (9 Cin + K2) per launch, pixels = the output patches
+ * the launch computed, partial patches and padding included):
  * out[0] = convolution ms, out[1] = convolution FLOPs, out[2] = Gram ms, out[3] = other ms,
  * out[4] = convolution launches, out[5] = all kernel launches (counted with timing on or off).
  * Synchronizes `stream`. */
@@ -225,21 +226,29 @@ nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int 
  * chunks, reduced in FP64 in a fixed order (deterministic). dtype: NST_PREC_FP32 or
  * NST_PREC_BF16 elements; C a multiple of 64, 64 <= C <= 512; 1 <= npix < 2^31. G_dev: C*C
  * doubles in device memory, overwritten. Scratch for the partial sums (at most 1,216 blocks of
- * 64 x 64 floats, 19 MiB) is allocated stream-ordered and released on `stream`. */
+ * 64 x 64 floats, 19 MiB) is allocated stream-ordered and released on `stream`. Bad arguments
+ * (including C outside 64..512 or not a multiple of 64) give NST_ERR_INVALID_ARG. */
 nst_status nst_gram(int dtype, const void *V_dev, long long npix, int C, double *G_dev,
                     void *stream);
 
 /* ---- Gram statistics without device allocation ----------------------------------------------
- * The paper has no counterpart: this is a library convenience. Same result and kernels as
- * nst_gram, for callers that may not allocate device memory themselves (for example a plugin
- * inside an application whose own pool allocator owns the GPU, where cudaMalloc/cudaFree would
- * synchronize the device and bypass the pool). The chunk partial sums go to a fixed 16 MiB array
- * inside libnst's device image instead of allocated scratch; every GPU that loads the library
- * keeps that array until the process exits. The call allocates nothing.
- *   - dtype, V_dev, npix, G_dev as for nst_gram; C must be a multiple of 64 with 64 <= C <= 512
- *     (the per-chunk block pairs must fit the array): otherwise NST_ERR_SHAPE, nothing launched.
- *   - The first call on each device looks up the array's device address (with that device
- *     current); make that first call before any stream capture.
+ * The paper has no counterpart: this is a library convenience. Same kernels and the same chunk
+ * plan as nst_gram, so the result is bitwise identical to nst_gram's on the same input, for
+ * callers that may not allocate device memory themselves (for example a plugin inside an
+ * application whose own pool allocator owns the GPU, where cudaMalloc/cudaFree would
+ * synchronize the device and bypass the pool). The chunk partial sums go to a fixed 19 MiB
+ * array (1,216 blocks of 64 x 64 floats) inside libnst's device image instead of allocated
+ * scratch; every GPU that loads the library keeps that array until the process exits. The call
+ * allocates nothing.
+ *   - dtype, V_dev, npix, G_dev as for nst_gram. C must be a multiple of 64, at least 64
+ *     (otherwise NST_ERR_INVALID_ARG, as nst_gram); C > 512 is beyond the array's maximum and
+ *     gives NST_ERR_SHAPE. Nothing is launched on either error; nst_last_error(NULL) says why.
+ *   - A CUDA error still pending from earlier work when the call starts is returned as
+ *     NST_ERR_CUDA (and cleared) before anything is launched.
+ *   - The array's device address is looked up once per device and CUDA context, with that
+ *     device current (again after cudaDeviceReset or when another context becomes current). The
+ *     first call on each device (and context) does that look-up: make it before any stream
+ *     capture.
  *   - All calls share the one array and it keeps the previous call's contents: calls whose work
  *     overlaps on the GPU (different streams, or different threads) race and corrupt each other;
  *     serialize them on one stream. */

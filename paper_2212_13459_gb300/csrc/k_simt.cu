@@ -437,28 +437,46 @@ __global__ void unpool_kernel(const T *__restrict__ gp, const T *__restrict__ ac
 // set (the ReLU gate is shut). One 32-bit word per 8 channels c .. c+7 at byte (p C + c) / 2,
 // channel c+k in the nibble at bit 8 (k & 3) + 4 (k >> 2). The backward reads half a byte per
 // value instead of the four activations.
+// rects (optional): per block, the pooled rectangle {y0, y1, x0, x1} to route (the rest of the
+// block's full-resolution gradient is left as it is); grid (n, B), row b = block b. Without
+// rects: every pooled position of the buffer, grid-stride over all blocks.
 __global__ void unpool_idx_kernel(const __nv_bfloat16 *__restrict__ gp,
                                   const unsigned char *__restrict__ idx,
                                   __nv_bfloat16 *__restrict__ g, int B, int Hp, int Wp, int C,
-                                  const BlockGeom *__restrict__ geom, int level_out) {
+                                  const BlockGeom *__restrict__ geom, int level_out,
+                                  const int4 *__restrict__ rects) {
   const int C8 = C / 8;
-  const long long n = (long long)B * Hp * Wp * C8;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  int4 r = make_int4(0, Hp, 0, Wp);
+  long long n = (long long)B * Hp * Wp * C8;
+  long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (rects) {
+    r = rects[blockIdx.y];
+    n = (long long)max(0, r.y - r.x) * max(0, r.w - r.z) * C8;
+  }
+  const int rw = r.w - r.z;
+  for (long long i = i0; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(i % C8) * 8;
-    long long p = i / C8;
-    const int x = (int)(p % Wp);
-    const int y = (int)((p / Wp) % Hp);
-    const int b = (int)(p / ((long long)Wp * Hp));
+    const long long q = i / C8;
+    int x, y, b;
+    if (rects) {
+      x = r.z + (int)(q % rw);
+      y = r.x + (int)(q / rw);
+      b = blockIdx.y;
+    } else {
+      x = (int)(q % Wp);
+      y = (int)((q / Wp) % Hp);
+      b = (int)(q / ((long long)Wp * Hp));
+    }
+    const long long p = ((long long)b * Hp + y) * Wp + x;
     const BlockGeom gm = geom[b];
     const int Wi = 2 * Wp;
     const size_t o0 = (((size_t)b * 2 * Hp + 2 * y) * Wi + 2 * x) * C + c;
     const size_t offs[4] = {o0, o0 + C, o0 + (size_t)Wi * C, o0 + (size_t)Wi * C + C};
-    float r[4][8];
+    float rv[4][8];
 #pragma unroll
     for (int k = 0; k < 4; k++)
 #pragma unroll
-      for (int j = 0; j < 8; j++) r[k][j] = 0.f;
+      for (int j = 0; j < 8; j++) rv[k][j] = 0.f;
     if (y < (gm.eh >> level_out) && x < (gm.ew >> level_out)) {
       float gv[8];
       load8(gp + (size_t)p * C + c, gv);
@@ -468,11 +486,11 @@ __global__ void unpool_idx_kernel(const __nv_bfloat16 *__restrict__ gp,
         const uint32_t nib = (w >> (8 * (j & 3) + 4 * (j >> 2))) & 0xfu;
         const uint32_t first = nib & (0u - nib);   // lowest set bit, 0 if none
 #pragma unroll
-        for (int q = 0; q < 4; q++) r[q][j] = first == (1u << q) ? gv[j] : 0.f;
+        for (int qq = 0; qq < 4; qq++) rv[qq][j] = first == (1u << qq) ? gv[j] : 0.f;
       }
     }
 #pragma unroll
-    for (int k = 0; k < 4; k++) store8(g + offs[k], r[k]);
+    for (int k = 0; k < 4; k++) store8(g + offs[k], rv[k]);
   }
 }
 
@@ -495,9 +513,18 @@ void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C
 }
 void launch_unpool_idx(const __nv_bfloat16 *gp, const unsigned char *idx, __nv_bfloat16 *g,
                        int B, int Hp, int Wp, int C, const BlockGeom *geom, int level_out,
-                       cudaStream_t s) {
+                       const int4 *rects, int max_rect_px, cudaStream_t s) {
+  if (rects) {
+    if (max_rect_px <= 0) return;
+    const long long per = (long long)max_rect_px * C / 8;
+    int nx = (int)std::min<long long>((per + 255) / 256, std::max(1, 152 * 32 / B));
+    dim3 grid(nx, B);
+    unpool_idx_kernel<<<grid, 256, 0, s>>>(gp, idx, g, B, Hp, Wp, C, geom, level_out, rects);
+    return;
+  }
   unpool_idx_kernel<<<ew_grid((long long)B * Hp * Wp * C / 8), 256, 0, s>>>(gp, idx, g, B, Hp, Wp,
-                                                                            C, geom, level_out);
+                                                                            C, geom, level_out,
+                                                                            nullptr);
 }
 template void launch_pool<float>(const float *, float *, int, int, int, int, const BlockGeom *,
                                  int, cudaStream_t);

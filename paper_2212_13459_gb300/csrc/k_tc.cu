@@ -47,6 +47,24 @@ struct TcGeom {
   int cin_blocks;       // cin / 64
 };
 
+// Origin of output patch (M tile) mt: from the launch's patch list when it has one (each
+// block's needed rectangle only), else patch (mt % tiles_x, mt / tiles_x) of block
+// mt / (tiles_x tiles_y) on the regular grid over the whole buffer.
+__device__ __forceinline__ void patch_origin(const ConvArgs &a, const TcGeom &tg, int mt, int &b,
+                                             int &y0, int &x0) {
+  if (a.tiles) {
+    const int4 t = __ldg(a.tiles + mt);
+    b = t.x;
+    y0 = t.y;
+    x0 = t.z;
+  } else {
+    const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
+    b = mt / (tg.tiles_x * tg.tiles_y);
+    y0 = ty * tg.TH;
+    x0 = tx * tg.TW;
+  }
+}
+
 // Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n.
 __host__ __device__ constexpr uint32_t make_idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
@@ -150,48 +168,53 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
 // The four pixels of a pooling window are rows (y, x), (y, x+1), (y+1, x), (y+1, x+1) of the
 // output patch. With 8- or 16-pixel-wide patches and 32 rows per epilogue warp they sit in one
 // warp at lanes l, l^1, l^TW, l^(TW+1): the max is two shuffles, and the window's top-left lane
-// writes the pooled value (the BF16 values, exactly as stored, so the result equals pooling the
-// stored activation). Outside the block's valid pooled region the pooled map is zero.
+// writes the pooled value. Outside the block's valid pooled region the pooled map is zero.
+//
+// The decision is taken on the FP32 activations (accumulator + bias, ReLU), before they are
+// rounded for storage: rounding to BF16 merges values that differ by less than half an ulp
+// (2^-9 relative), which at a smooth input would turn most windows into exact ties. The pooled
+// value is the window max rounded once to BF16; as rounding is monotone, that equals pooling
+// the rounded activations.
 //
 // Window positions for the backward (pool_idx, when a backward pass follows): 4 bits per pooled
 // value, bit q set when window pixel q (row-major: 0 = (y, x), 1 = (y, x+1), 2 = (y+1, x),
-// 3 = (y+1, x+1)) equals the window max and that max is positive. The gradient goes to the lowest
-// set bit, the first maximum, as in routing by the stored activations; no bit = the ReLU gate is
-// shut. Layout: one 32-bit word per 8 channels c .. c+7 at byte (pooled pixel * C + c) / 2, the
-// nibble of channel c+k at bit 8 (k & 3) + 4 (k >> 2).
+// 3 = (y+1, x+1)) equals the FP32 window max and that max is positive. The gradient goes to the
+// lowest set bit, the first maximum; no bit = the ReLU gate is shut. Layout: one 32-bit word per
+// 8 channels c .. c+7 at byte (pooled pixel * C + c) / 2, the nibble of channel c+k at bit
+// 8 (k & 3) + 4 (k >> 2).
 __device__ __forceinline__ uint32_t pool_nibble_shift(int k) { return 8 * (k & 3) + 4 * (k >> 2); }
 
 __device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGeom &g, int b,
                                                 int y, int x, int n, int tw, const float *v) {
   constexpr int NC = 32, NW = NC / 2;   // channels, BF16 pairs
-  // the stored BF16 values, two channels per register; max over the window with 2 shuffles,
-  // which leave the max in all four lanes of the window
-  uint32_t h[NW], eq[NW];
-  const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
+  // FP32 max over the window with 2 shuffles per channel, which leave it in all four lanes
+  float m[NC];
 #pragma unroll
-  for (int j = 0; j < NW; j++) {
-    const __nv_bfloat162 own = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-    const uint32_t ou = *reinterpret_cast<const uint32_t *>(&own);
-    uint32_t o1 = __shfl_xor_sync(0xffffffffu, ou, 1);
-    __nv_bfloat162 m = __hmax2(own, *reinterpret_cast<__nv_bfloat162 *>(&o1));
-    uint32_t mu = *reinterpret_cast<uint32_t *>(&m);
-    uint32_t o2 = __shfl_xor_sync(0xffffffffu, mu, tw);
-    m = __hmax2(m, *reinterpret_cast<__nv_bfloat162 *>(&o2));
-    h[j] = *reinterpret_cast<uint32_t *>(&m);
-    if (a.pool_idx) eq[j] = __heq2_mask(own, m) & __hgt2_mask(m, zero2);   // 0xffff: flagged
+  for (int j = 0; j < NC; j++) {
+    const float m1 = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+    m[j] = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, tw));
   }
   uint32_t idx[NC / 8];
   if (a.pool_idx) {
-    const uint32_t qbit = 0x11111111u << ((x & 1) | ((y & 1) << 1));
+    const int qpos = (x & 1) | ((y & 1) << 1);
 #pragma unroll
     for (int i = 0; i < NC / 8; i++) {
-      const uint32_t lo = __byte_perm(eq[4 * i], eq[4 * i + 1], 0x6420);      // channels 0..3
-      const uint32_t hi = __byte_perm(eq[4 * i + 2], eq[4 * i + 3], 0x6420);  // channels 4..7
-      uint32_t w = ((lo & 0x0f0f0f0fu) | (hi & 0xf0f0f0f0u)) & qbit;
+      uint32_t w = 0u;
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        w |= (v[8 * i + k] == m[8 * i + k] && m[8 * i + k] > 0.f) ? 1u << pool_nibble_shift(k)
+                                                                   : 0u;
+      w <<= qpos;
       w |= __shfl_xor_sync(0xffffffffu, w, 1);
       w |= __shfl_xor_sync(0xffffffffu, w, tw);
       idx[i] = w;
     }
+  }
+  uint32_t h[NW];
+#pragma unroll
+  for (int j = 0; j < NW; j++) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(m[2 * j], m[2 * j + 1]);
+    h[j] = *reinterpret_cast<const uint32_t *>(&p);
   }
   if ((y & 1) || (x & 1) || y >= a.Hb || x >= a.Wb) return;
   const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
@@ -265,17 +288,18 @@ __device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g,
 }
 
 // fused 2 x 2 max pool of a 32-pixel chunk (whole rows of a patch 8 or 16 wide) from the warp's
-// transpose tile: lane = (window, 8-channel group); the window's four values are recomputed
-// exactly as the forward epilogue stored them (bias, ReLU, valid region, BF16 rounding)
-__device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g, int b, int tx,
-                                           int ty, const TcGeom &tg, int c, int n,
+// transpose tile: lane = (window, 8-channel group); the window's four values are recomputed in
+// FP32 as the forward epilogue forms them (bias, ReLU, valid region), the first maximum is
+// decided on those FP32 values, and the max is rounded once to BF16 for the pooled map
+__device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g, int b,
+                                           int oy, int ox, const TcGeom &tg, int c, int n,
                                            const uint8_t *tsm) {
   const int lane = threadIdx.x & 31;
   const int w = lane >> 2, cg = lane & 3;
   const int wpr = tg.TW >> 1;   // windows per row pair
   const int j0 = 2 * (w / wpr) * tg.TW + 2 * (w % wpr);
   const int pp0 = c + j0;
-  const int y = ty * tg.TH + pp0 / tg.TW, x = tx * tg.TW + pp0 % tg.TW;
+  const int y = oy + pp0 / tg.TW, x = ox + pp0 % tg.TW;
   if (pp0 >= tg.TH * tg.TW || y >= a.Hb || x >= a.Wb) return;
   const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8));
   const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8 + 4));
@@ -294,8 +318,7 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
     swap_tile_read8(tsm, j, cg, r);
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      const float s = __bfloat162float(__float2bfloat16_rn(valid ? fmaxf(r[i] + bb[i], 0.f)
-                                                                 : 0.f));
+      const float s = valid ? fmaxf(r[i] + bb[i], 0.f) : 0.f;
       if (qq == 0 || s > m[i] || (s == m[i] && q < k8[i])) {
         m[i] = s;
         k8[i] = q;
@@ -369,9 +392,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
         const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
-        const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
-        const int b = mt / (tg.tiles_x * tg.tiles_y);
-        const int x0 = tx * tg.TW, y0 = ty * tg.TH, n0 = nt * BN;
+        int b, y0, x0;
+        patch_origin(a, tg, mt, b, y0, x0);
+        const int n0 = nt * BN;
         for (int kb = 0; kb < kb_total; kb++) {
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
             ok = false;
@@ -442,8 +465,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!__shfl_sync(0xffffffffu, ready, 0)) break;
       tc_fence_after();
       const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
-      const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
-      const int b = mt / (tg.tiles_x * tg.tiles_y);
+      int b, oy, ox;
+      patch_origin(a, tg, mt, b, oy, ox);
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
       const int cg = lane & 3;
@@ -460,14 +483,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < 4; k++) {
           const int j = k * 8 + (lane >> 2);
           const int pp = q * 32 + j;
-          const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
+          const int y = oy + pp / tg.TW, x = ox + pp % tg.TW;
           if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb) {
             float r[8];
             swap_tile_read8(tsm, j, cg, r);
             epilogue8(a, g, b, y, x, nt * BN + c + cg * 8, r);
           }
         }
-        if (a.pool_out) swap_pool8(a, g, b, tx, ty, tg, q * 32, nt * BN + c, tsm);
+        if (a.pool_out) swap_pool8(a, g, b, oy, ox, tg, q * 32, nt * BN + c, tsm);
         __syncwarp();
       }
       tc_fence_before();
@@ -576,8 +599,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       bool ok = true;
       for (int t = m_first; t < m_total && ok; t += m_step) {
-        const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
-        const int b = t / (tg.tiles_x * tg.tiles_y);
+        int b, oy, ox;
+        patch_origin(a, tg, t, b, oy, ox);
         for (int kb = 0; kb < KBT; kb++) {
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
             ok = false;
@@ -587,9 +610,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_expect_tx(fb, kHaloBoxBytes);
           const uint32_t sa = a_base + stage * kHaloStage;
           if (kb < KB)
-            tma_load_4d(sa, &tmA, fb, kb * kBK, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
+            tma_load_4d(sa, &tmA, fb, kb * kBK, ox - 1, oy - 1, b);
           else
-            tma_load_4d(sa, &tmA2, fb, (kb - KB) * kBK, tx * kHaloTW - 1, ty * kHaloTH - 1, b);
+            tma_load_4d(sa, &tmA2, fb, (kb - KB) * kBK, ox - 1, oy - 1, b);
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
       }
@@ -668,9 +691,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) ready = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err);
       if (!__shfl_sync(0xffffffffu, ready, 0)) break;
       tc_fence_after();
-      const int tx = t % tg.tiles_x, ty = (t / tg.tiles_x) % tg.tiles_y;
-      const int b = t / (tg.tiles_x * tg.tiles_y);
-      const int y = ty * kHaloTH + row / kHaloTW, x = tx * kHaloTW + row % kHaloTW;
+      int b, oy, ox;
+      patch_origin(a, tg, t, b, oy, ox);
+      const int y = oy + row / kHaloTW, x = ox + row % kHaloTW;
       const bool inb = y < a.Hb && x < a.Wb;
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
@@ -785,9 +808,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
         const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
-        const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
-        const int b = mt / (tg.tiles_x * tg.tiles_y);
-        const int x0 = tx * tg.TW, y0 = ty * tg.TH, n0 = nt * kSwapBN;
+        int b, y0, x0;
+        patch_origin(a, tg, mt, b, y0, x0);
+        const int n0 = nt * kSwapBN;
         for (int kb = 0; kb < kb_total; kb++) {
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
             ok = false;
@@ -857,8 +880,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!__shfl_sync(0xffffffffu, ready, 0)) break;
       tc_fence_after();
       const int nt = t % tg.n_tiles, mt = t / tg.n_tiles;
-      const int tx = mt % tg.tiles_x, ty = (mt / tg.tiles_x) % tg.tiles_y;
-      const int b = mt / (tg.tiles_x * tg.tiles_y);
+      int b, oy, ox;
+      patch_origin(a, tg, mt, b, oy, ox);
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kSwapBP);
       const int n = nt * kSwapBN + q * 32;
@@ -881,10 +904,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           float r[8];
           swap_tile_read8(tsm, j, cg, r);
           const int pp = c + j;
-          const int y = ty * tg.TH + pp / tg.TW, x = tx * tg.TW + pp % tg.TW;
+          const int y = oy + pp / tg.TW, x = ox + pp % tg.TW;
           if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb) epilogue8(a, g, b, y, x, n + cg * 8, r);
         }
-        if (a.pool_out) swap_pool8(a, g, b, tx, ty, tg, c, n, tsm);
+        if (a.pool_out) swap_pool8(a, g, b, oy, ox, tg, c, n, tsm);
         __syncwarp();
       }
       tc_fence_before();
@@ -1007,18 +1030,22 @@ cudaError_t launch_swap(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   return cudaGetLastError();
 }
 
-// Output patch of at most `rows` pixels (the tile's M or N) covering an H x W map with the fewest
-// tiles. Without fused pooling any TH x TW <= rows works (a 9 x 14 patch tiles an 84 x 98 map
-// with 97 % of the MMA rows in use where 8 x 16 reaches 83 %); with fused pooling the 2 x 2
-// windows must pair up inside a 32-pixel epilogue chunk, so TW is 8 or 16 and TH * TW = rows.
-void pick_patch_rows(int H, int W, int rows, int &TH, int &TW, bool pool) {
+// Output patch of at most `rows` pixels (the tile's M or N) covering n rectangles h[i] x w[i]
+// with the fewest tiles. Without fused pooling any TH x TW <= rows works (a 9 x 14 patch tiles
+// an 84 x 98 map with 97 % of the MMA rows in use where 8 x 16 reaches 83 %); with fused pooling
+// the 2 x 2 windows must pair up inside a 32-pixel epilogue chunk, so TW is 8 or 16 and
+// TH * TW = rows.
+void pick_patch_multi(const int *h, const int *w, int n, int rows, bool pool, int &TH, int &TW) {
   long long best_tiles = -1;
   int best_area = 0;
+  TH = 1;
+  TW = rows;
   for (int th = 1; th <= rows && th <= 256; th++) {
     const int tw = rows / th;
     if (tw < 1 || tw > 256) continue;
     if (pool && !((tw == 8 || tw == 16) && th * tw == rows)) continue;
-    const long long tiles = (long long)((H + th - 1) / th) * ((W + tw - 1) / tw);
+    long long tiles = 0;
+    for (int i = 0; i < n; i++) tiles += (long long)((h[i] + th - 1) / th) * ((w[i] + tw - 1) / tw);
     if (best_tiles < 0 || tiles < best_tiles || (tiles == best_tiles && th * tw > best_area)) {
       best_tiles = tiles;
       best_area = th * tw;
@@ -1026,6 +1053,10 @@ void pick_patch_rows(int H, int W, int rows, int &TH, int &TW, bool pool) {
       TW = tw;
     }
   }
+}
+
+void pick_patch_rows(int H, int W, int rows, int &TH, int &TW, bool pool) {
+  pick_patch_multi(&H, &W, 1, rows, pool, TH, TW);
 }
 
 template <int BN, int KB, int P2KB, int NT, bool MASK_SMEM = false>
@@ -1048,7 +1079,9 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   tg.tiles_x = (a.Wb + kHaloTW - 1) / kHaloTW;
   tg.tiles_y = (a.Hb + kHaloTH - 1) / kHaloTH;
   tg.n_tiles = NT;
-  tg.total = a.B * tg.tiles_x * tg.tiles_y;   // M tiles; every slice covers all of them
+  // M tiles; every slice covers all of them
+  tg.total = a.tiles ? a.n_mtiles : a.B * tg.tiles_x * tg.tiles_y;
+  if (tg.total <= 0) return cudaSuccess;
   int grid = std::min(tg.total * NT, g_num_sms);
   grid = std::max(NT, grid / NT * NT);
   conv_tc_halo_kernel<BN, KB, P2KB, NT, MASK_SMEM><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2,
@@ -1126,23 +1159,58 @@ cudaError_t launch_timeout_check(long long limit_cycles, unsigned *err, cudaStre
   return cudaGetLastError();
 }
 
+void conv_tc_patch_rule(int cin, int cout, int taps, int k2, int *rows, bool *fixed) {
+  ConvArgs a{};
+  a.cin = taps ? cin : 0;
+  a.cout = cout;
+  a.taps = taps;
+  a.k2 = k2;
+  int bn, kb, p2, nt;
+  *fixed = halo_shape(a, &bn, &kb, &p2, &nt);
+  *rows = *fixed ? kHaloTH * kHaloTW : (cout == kSwapBN ? kSwapBP : 128);
+}
+
+void conv_tc_pick_patch(const int *h, const int *w, int n, int rows, bool fixed, bool pool,
+                        int *TH, int *TW) {
+  if (fixed) {
+    *TH = kHaloTH;
+    *TW = kHaloTW;
+    return;
+  }
+  pick_patch_multi(h, w, n, rows, pool, *TH, *TW);
+}
+
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   if (!tc_available()) return cudaErrorNotSupported;
   if ((a.taps != 0 && a.taps != 9) || a.cout % 64 || (a.taps && a.cin % 64) || a.k2 % 64 ||
       (a.taps == 0 && a.k2 == 0))
     return cudaErrorInvalidValue;
   int hBN, hKB, hP2, hNT;
-  if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
+  if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) {
+    if (a.tiles && (a.TH != kHaloTH || a.TW != kHaloTW)) return cudaErrorInvalidValue;
+    return launch_conv_tc_halo(a, hBN, hKB, hP2, hNT, s);
+  }
   // 128 output channels: pixels as the MMA's N (256 wide) instead of channels (128 wide)
   const bool swap = a.cout == kSwapBN;
   const int BN = swap ? kSwapBN : (a.cout >= 256 ? 256 : a.cout);
+  const int rows = swap ? kSwapBP : 128;
   TcGeom tg;
-  pick_patch_rows(a.Hb, a.Wb, swap ? kSwapBP : 128, tg.TH, tg.TW, a.pool_out != nullptr);
+  if (a.tiles) {
+    // a patch list from the caller: its patch shape must follow this kernel's rule
+    if (a.TH < 1 || a.TW < 1 || a.TH * a.TW > rows ||
+        (a.pool_out && !((a.TW == 8 || a.TW == 16) && a.TH * a.TW == rows)))
+      return cudaErrorInvalidValue;
+    tg.TH = a.TH;
+    tg.TW = a.TW;
+  } else {
+    pick_patch_rows(a.Hb, a.Wb, rows, tg.TH, tg.TW, a.pool_out != nullptr);
+  }
   tg.tx_bytes = tg.TH * tg.TW * kBK * 2 + BN * kBK * 2;
   tg.tiles_x = (a.Wb + tg.TW - 1) / tg.TW;
   tg.tiles_y = (a.Hb + tg.TH - 1) / tg.TH;
   tg.n_tiles = a.cout / BN;
-  tg.total = a.B * tg.tiles_x * tg.tiles_y * tg.n_tiles;
+  tg.total = (a.tiles ? a.n_mtiles : a.B * tg.tiles_x * tg.tiles_y) * tg.n_tiles;
+  if (tg.total <= 0) return cudaSuccess;
   tg.cin_blocks = a.taps ? a.cin / kBK : 0;
   tg.kb_main = a.taps * tg.cin_blocks;
   tg.kb2 = a.k2 / kBK;

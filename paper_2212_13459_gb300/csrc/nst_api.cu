@@ -107,8 +107,22 @@ void owned(int i0, int i1, int s, int n_glob, int &j0, int &j1) {
 constexpr int kOwnSlots = 7;
 constexpr int kOwnContent = 5, kOwnInner = 6;
 
+// One tensor-core convolution launch's patch list: entries [off, off + n) of the plan's patch
+// table, TH x TW patches.
+struct PatchList {
+  int off, n, TH, TW;
+};
+// The passes whose convolutions are restricted to what the owned pixels need (see needed_axis):
+// Step-1 statistics (also the style targets), the content target, the Step-2 forward.
+enum FwdKind { kFwdStats = 0, kFwdContent = 1, kFwdStep2 = 2, kFwdKinds = 3 };
+
 struct Batch {
   int t0, B;                                  // first block index, block count
+  PatchList fwd[kFwdKinds][kNConv];           // forward conv l (l >= 1) per pass kind
+  PatchList bwd[kNConv];                      // input-gradient conv l (l >= 1)
+  PatchList vr;                               // the V R seed of conv5_1's gradient
+  PatchList unpool[kNConv];                   // pooled layer l: one pooled rectangle per block
+                                              // ({y0, y1, x0, x1}; TH = largest area)
   int chunk_off[kNStyle + 1], nchunks[kNStyle + 1];  // Gram chunks per style layer; [5] content
   int tc_off[kNStyle], tc_runs[kNStyle];      // tensor-core Gram runs per style layer
   int max_inner_px, max_content_px;
@@ -132,6 +146,7 @@ struct PassPlan {
   CUtensorMap *d_maps = nullptr;   // [kNStyle][ntiles]
   const void *maps_ws = nullptr;   // workspace the maps were encoded for
   std::vector<OwnRect> own_host;   // [kOwnSlots][ntiles]
+  int4 *d_patches = nullptr;       // patch table of every launch of every batch
 };
 
 struct Workspace {
@@ -141,6 +156,8 @@ struct Workspace {
 };
 
 }  // namespace
+
+void nst::set_last_error_msg(const char *msg) { set_global_err(msg ? msg : ""); }
 
 struct nst_ctx {
   int device = 0;
@@ -274,6 +291,99 @@ size_t tile_bytes(int Hb, int Wb, size_t esz, bool pool_positions) {
   return tot;
 }
 
+// ---- needed rectangles ----------------------------------------------------------------------------
+// The owned (inner) pixels of a block depend, at each layer, only on a rectangle of that layer's
+// map that grows with the receptive field: Step 1 needs ReLU5_1 on the owned pixels only, and
+// each earlier layer one pixel more per 3x3 convolution (twice that across a pooling); Step 2's
+// backward needs dE/dReLU1_1 on the inner pixels +- 1 and one pixel more per convolution going
+// deeper; its forward needs the activations where the backward reads them (ReLU masks, V of
+// V R, the pooling windows, the content feature) plus the forward reach of the deeper layers.
+// Each convolution therefore computes only those rectangles of each block, not the whole
+// extended block: the values there are the same sums of the same inputs in the same order, so
+// E and dE/dx are unchanged, bit for bit. Intervals are per axis (every step is separable),
+// half-open, in global feature coordinates of their level.
+struct Iv {
+  int a, b;
+  bool empty() const { return b <= a; }
+};
+Iv iv_inter(Iv p, Iv q) { return {std::max(p.a, q.a), std::min(p.b, q.b)}; }
+Iv iv_union(Iv p, Iv q) {
+  if (p.empty()) return q;
+  if (q.empty()) return p;
+  return {std::min(p.a, q.a), std::max(p.b, q.b)};
+}
+Iv iv_grow(Iv p, int d) { return p.empty() ? p : Iv{p.a - d, p.b + d}; }
+Iv iv_pooldown(Iv p) { return p.empty() ? p : Iv{p.a >> 1, ((p.b - 1) >> 1) + 1}; }   // windows
+Iv iv_poolup(Iv p) { return p.empty() ? p : Iv{2 * p.a, 2 * p.b}; }                    // pixels
+
+struct AxisNeed {
+  Iv F[kFwdKinds][kNConv];   // forward: outputs of conv l needed, per pass kind
+  Iv D[kNConv];              // backward: input gradient of conv l (level of conv l)
+  Iv G12;                    // backward seed: gradient of conv5_1's output
+};
+
+void needed_axis(int L, int i0, int i1, int e0, int e1, AxisNeed &n) {
+  Iv val[5], own[5];
+  for (int lv = 0; lv < 5; lv++) {
+    val[lv] = {e0 >> lv, e1 >> lv};
+    int j0, j1;
+    owned(i0, i1, 1 << lv, L >> lv, j0, j1);
+    own[lv] = {j0, j1};
+  }
+  // backward: G[l] = gradient of conv l's output, D[l] = conv l's input gradient
+  Iv G[kNConv];
+  G[0] = iv_inter(iv_grow(Iv{i0, i1}, 1), val[0]);
+  n.D[0] = Iv{0, 0};
+  for (int l = 1; l < kNConv; l++) {
+    const int lv = kLevel[l];
+    n.D[l] = kPoolAfter[l - 1] ? iv_inter(iv_pooldown(G[l - 1]), val[lv]) : G[l - 1];
+    G[l] = iv_inter(iv_grow(n.D[l], 1), val[lv]);
+  }
+  n.G12 = G[kNConv - 1];
+  for (int k = 0; k < kFwdKinds; k++) {
+    const int last = k == kFwdContent ? kContentConv : kNConv - 1;
+    for (int l = 0; l < kNConv; l++) n.F[k][l] = Iv{0, 0};
+    for (int l = last; l >= 0; l--) {
+      const int lv = kLevel[l];
+      Iv need{0, 0};
+      bool style = false;
+      for (int si = 0; si < kNStyle; si++) style |= kStyleConv[si] == l;
+      if (k != kFwdContent && style) need = own[lv];                  // Gram of the owned pixels
+      if (k == kFwdContent && l == kContentConv) need = own[lv];      // the content target
+      if (k == kFwdStep2) {
+        need = iv_union(need, G[l]);                                  // masks, V R, content
+        if (l == kContentConv) need = iv_union(need, own[lv]);        // content loss
+        if (kPoolAfter[l] && l < last) need = iv_union(need, iv_poolup(n.D[l + 1]));  // routing
+      }
+      if (l < last) {   // the next convolution's input, one pixel around what it computes
+        if (kPoolAfter[l])
+          need = iv_union(need, iv_poolup(iv_inter(iv_grow(n.F[k][l + 1], 1), val[lv + 1])));
+        else
+          need = iv_union(need, iv_inter(iv_grow(n.F[k][l + 1], 1), val[lv]));
+      }
+      n.F[k][l] = iv_inter(need, val[lv]);
+    }
+  }
+}
+
+// One block's rectangle of a launch in its buffer ([0, buf) at the launch's level; the valid
+// extent is [0, ext)): global interval -> block-local, and a rectangle that reaches the valid
+// extent runs on to the buffer's end, so the launch also writes the zeros past the block's edge
+// that the next layer reads as padding. With fused pooling (pool) the ends are even (whole
+// windows) and the edge is that of the pooled map: the last whole window ends at ext & ~1 (floor
+// pooling drops an odd last pixel), and the windows after it give the pooled map's zeros.
+Iv local_rect(Iv g, int e0_level, int ext, int buf, bool pool) {
+  if (g.empty()) return Iv{0, 0};
+  Iv r{g.a - e0_level, g.b - e0_level};
+  if (pool) {
+    r.a &= ~1;
+    r.b = (r.b + 1) & ~1;
+    ext &= ~1;
+  }
+  if (r.b >= ext) r.b = buf;
+  return iv_inter(r, Iv{0, buf});
+}
+
 nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
   auto key = std::make_tuple(H, W, ctx->cfg.tiles_h, ctx->cfg.tiles_w, margin);
   auto it = ctx->plans.find(key);
@@ -387,7 +497,86 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
     }
     p.batches.push_back(bt);
   }
+  // patch tables of the tensor-core convolutions: per batch, per launch, each block's needed
+  // rectangle covered by patches of the launch's shape
+  std::vector<AxisNeed> ny(nt), nx(nt);
+  for (int i = 0; i < nt; i++) {
+    const Tile &t = p.tiles[i];
+    needed_axis(H, t.iy0, t.iy1, t.ey0, t.ey1, ny[i]);
+    needed_axis(W, t.ix0, t.ix1, t.ex0, t.ex1, nx[i]);
+  }
+  std::vector<int4> patches;
+  auto add_list = [&](const Batch &bt, int level, int cin, int cout, int taps, int k2, bool pool,
+                      auto pick) -> PatchList {
+    PatchList pl{(int)patches.size(), 0, 0, 0};
+    int rows;
+    bool fixed;
+    conv_tc_patch_rule(cin, cout, taps, k2, &rows, &fixed);
+    std::vector<Iv> ry(bt.B), rx(bt.B);
+    std::vector<int> hs(bt.B), wsz(bt.B);
+    for (int j = 0; j < bt.B; j++) {
+      const Tile &t = p.tiles[bt.t0 + j];
+      Iv gy, gx;
+      pick(bt.t0 + j, gy, gx);
+      ry[j] = local_rect(gy, t.ey0 >> level, (t.ey1 - t.ey0) >> level, p.Hb >> level, pool);
+      rx[j] = local_rect(gx, t.ex0 >> level, (t.ex1 - t.ex0) >> level, p.Wb >> level, pool);
+      hs[j] = std::max(0, ry[j].b - ry[j].a);
+      wsz[j] = std::max(0, rx[j].b - rx[j].a);
+    }
+    conv_tc_pick_patch(hs.data(), wsz.data(), bt.B, rows, fixed, pool, &pl.TH, &pl.TW);
+    for (int j = 0; j < bt.B; j++)
+      for (int y = ry[j].a; y < ry[j].b; y += pl.TH)
+        for (int x = rx[j].a; x < rx[j].b; x += pl.TW) patches.push_back(make_int4(j, y, x, 0));
+    pl.n = (int)patches.size() - pl.off;
+    return pl;
+  };
+  for (Batch &bt : p.batches) {
+    for (int k = 0; k < kFwdKinds; k++)
+      for (int l = 1; l < kNConv; l++)
+        bt.fwd[k][l] = add_list(bt, kLevel[l], kCin[l], kCout[l], 9, 0, kPoolAfter[l],
+                                [&](int i, Iv &gy, Iv &gx) {
+                                  gy = ny[i].F[k][l];
+                                  gx = nx[i].F[k][l];
+                                });
+    for (int l = 1; l < kNConv; l++) {
+      const int lp = l - 1;
+      int k2 = 0;
+      for (int si = 0; si < kNStyle; si++)
+        if (kStyleConv[si] == lp && !kPoolAfter[lp]) k2 = kCout[lp];
+      bt.bwd[l] = add_list(bt, kLevel[l], kCout[l], kCin[l], 9, k2, false,
+                           [&](int i, Iv &gy, Iv &gx) {
+                             gy = ny[i].D[l];
+                             gx = nx[i].D[l];
+                           });
+    }
+    bt.vr = add_list(bt, kLevel[kNConv - 1], 0, kCout[kNConv - 1], 0, kCout[kNConv - 1], false,
+                     [&](int i, Iv &gy, Iv &gx) {
+                       gy = ny[i].G12;
+                       gx = nx[i].G12;
+                     });
+    // the unpool after pooled layer l routes the pooled gradient of the pooled positions that
+    // the next input-gradient convolution computed (D[l + 1]), with the same edge rule
+    for (int l = 0; l + 1 < kNConv; l++) {
+      if (!kPoolAfter[l]) continue;
+      const int lv = kLevel[l] + 1;
+      PatchList &pl = bt.unpool[l];
+      pl = PatchList{(int)patches.size(), bt.B, 0, 0};
+      for (int j = 0; j < bt.B; j++) {
+        const Tile &t = p.tiles[bt.t0 + j];
+        const Iv ry = local_rect(ny[bt.t0 + j].D[l + 1], t.ey0 >> lv, (t.ey1 - t.ey0) >> lv,
+                                 p.Hb >> lv, false);
+        const Iv rx = local_rect(nx[bt.t0 + j].D[l + 1], t.ex0 >> lv, (t.ex1 - t.ex0) >> lv,
+                                 p.Wb >> lv, false);
+        patches.push_back(make_int4(ry.a, std::max(ry.a, ry.b), rx.a, std::max(rx.a, rx.b)));
+        pl.TH = std::max(pl.TH, std::max(0, ry.b - ry.a) * std::max(0, rx.b - rx.a));
+      }
+    }
+  }
   // device copies (one-time per geometry; synchronous so host arrays may be dropped)
+  CK(cudaMalloc(&p.d_patches, sizeof(int4) * std::max<size_t>(1, patches.size())));
+  if (!patches.empty())
+    CK(cudaMemcpy(p.d_patches, patches.data(), sizeof(int4) * patches.size(),
+                  cudaMemcpyHostToDevice));
   CK(cudaMalloc(&p.d_geom, sizeof(BlockGeom) * nt));
   CK(cudaMalloc(&p.d_own, sizeof(OwnRect) * own.size()));
   CK(cudaMalloc(&p.d_chunks, sizeof(GramChunk) * std::max<size_t>(1, chunks.size())));
@@ -454,11 +643,22 @@ nst_status ensure_buffers(nst_ctx *ctx, const PassPlan &p, Workspace &ws) {
 }
 
 // ---- convolution dispatch -----------------------------------------------------------------------
+// the tensor-core engine computes only the launch's patch list (the CUDA-core engine ignores it
+// and computes whole blocks, with the same values where the list's patches lie)
+void use_patches(ConvArgs &a, const PassPlan &p, const PatchList &pl) {
+  a.tiles = p.d_patches + pl.off;
+  a.n_mtiles = pl.n;
+  a.TH = pl.TH;
+  a.TW = pl.TW;
+}
+
 nst_status run_conv(nst_ctx *ctx, ConvArgs a, cudaStream_t s) {
   a.err = ctx->d_err;
   ctx->launches++;
   ctx->conv_launches++;
-  ctx->conv_flops += 2.0 * a.B * (double)a.Hb * a.Wb * a.cout * ((double)a.taps * a.cin + a.k2);
+  const double px = ctx->use_tc && a.tiles ? (double)a.n_mtiles * a.TH * a.TW
+                                           : (double)a.B * a.Hb * a.Wb;
+  ctx->conv_flops += 2.0 * px * a.cout * ((double)a.taps * a.cin + a.k2);
   Timer tm(ctx, kTConv, s);
   if (ctx->use_tc) {
     cudaError_t e = launch_conv_tc(a, s);
@@ -488,11 +688,14 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
       launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);
     }
   }
+  const int kind = last_conv == kContentConv ? kFwdContent
+                                             : (for_backward ? kFwdStep2 : kFwdStats);
   for (int l = 1; l <= last_conv; l++) {
     const int lv = kLevel[l];
     ConvArgs a{};
     a.B = bt.B; a.Hb = p.Hb >> lv; a.Wb = p.Wb >> lv;
     a.cin = kCin[l]; a.cout = kCout[l]; a.taps = 9; a.k2 = 0;
+    use_patches(a, p, bt.fwd[kind][l]);
     a.A = kPoolAfter[l - 1] ? ws.pool[l - 1] : ws.act[l - 1];
     a.Wt = ctx->d_wf[l];
     a.out = ws.act[l];
@@ -612,6 +815,7 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
     a.mask = ws.act[l];
     a.geom = geom;
     a.level = lv;
+    use_patches(a, p, bt.vr);
     nst_status st = run_conv(ctx, a, s);
     if (st) return st;
   }
@@ -626,6 +830,7 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
     a.mode = kEpiBackward;
     a.geom = geom;
     a.level = lv;
+    use_patches(a, p, bt.bwd[l]);
     if (!kPoolAfter[lp]) {
       a.mask = ws.act[lp];
       for (int si = 0; si < kNStyle; si++)
@@ -651,7 +856,7 @@ nst_status backward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, cons
       if (ctx->use_tc)
         launch_unpool_idx((const __nv_bfloat16 *)ws.g[1 - cur], (const unsigned char *)ws.act[lp],
                           (__nv_bfloat16 *)ws.g[cur], bt.B, p.Hb >> lv, p.Wb >> lv, kCout[lp],
-                          geom, lv, s);
+                          geom, lv, p.d_patches + bt.unpool[lp].off, bt.unpool[lp].TH, s);
       else
         launch_unpool<T>((const T *)ws.g[1 - cur], (const T *)ws.act[lp], (T *)ws.g[cur], bt.B,
                          p.Hb >> lv, p.Wb >> lv, kCout[lp], geom, lv, s);
@@ -975,6 +1180,7 @@ nst_status nst_destroy(nst_ctx *ctx) {
     cudaFree(kv.second.d_chunks);
     cudaFree(kv.second.d_tcchunks);
     cudaFree(kv.second.d_maps);
+    cudaFree(kv.second.d_patches);
   }
   for (auto &ev : ctx->ev_pool) { cudaEventDestroy(ev.first); cudaEventDestroy(ev.second); }
   delete ctx;
@@ -1205,16 +1411,6 @@ nst_status nst_conv3x3(int dtype, int engine, int B, int H, int W, int cin, int 
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "nst_conv3x3");
   return NST_OK;
-}
-
-// chunking of a flat [npix][C] matrix: about 1,216 CTAs over the 64 x 64 block pairs
-static void gram_flat_plan(long long npix, int C, long long *chunk_len, int *nchunks) {
-  const int nb = C / 64, npairs = nb * (nb + 1) / 2;
-  const long long target = std::max(1, 1216 / npairs);
-  long long ch = std::max(256LL, (npix + target - 1) / target);
-  ch = (ch + 31) / 32 * 32;
-  *chunk_len = ch;
-  *nchunks = (int)((npix + ch - 1) / ch);
 }
 
 nst_status nst_gram(int dtype, const void *V, long long npix, int C, double *G, void *stream) {

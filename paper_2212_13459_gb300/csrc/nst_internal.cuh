@@ -80,6 +80,10 @@ struct ConvArgs {
                           // (alpha of the mean / std loss, Table 1 rows 3-4), or null
   unsigned char *pool_idx;  // forward with pool_out: also the window positions of the maximum,
                             // 4 bits per pooled value ([B][Hb/2][Wb/2][cout] / 2 bytes), or null
+  // tensor-core engine: the output patches to compute, one {block, y0, x0, 0} per patch (its
+  // origin in the block's [Hb][Wb] buffer), each TH x TW; null = every patch of the buffer
+  const int4 *tiles;
+  int n_mtiles, TH, TW;
 };
 
 }  // namespace nst

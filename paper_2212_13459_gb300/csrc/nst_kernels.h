@@ -58,10 +58,12 @@ void launch_pool(const T *in, T *out, int B, int Hp, int Wp, int C, const BlockG
 template <typename T>
 void launch_unpool(const T *gp, const T *act, T *g, int B, int Hp, int Wp, int C,
                    const BlockGeom *geom, int level_out, cudaStream_t s);
-// tensor-core form: routing by the window positions the fused forward pooling stored
+// tensor-core form: routing by the window positions the fused forward pooling stored; rects
+// (optional, device, one {y0, y1, x0, x1} of pooled positions per block, at most max_rect_px
+// positions each) restricts it to those positions
 void launch_unpool_idx(const __nv_bfloat16 *gp, const unsigned char *idx, __nv_bfloat16 *g,
                        int B, int Hp, int Wp, int C, const BlockGeom *geom, int level_out,
-                       cudaStream_t s);
+                       const int4 *rects, int max_rect_px, cudaStream_t s);
 template <typename T>
 void launch_gram_partial(const T *V, int Hb, int Wb, int C, const OwnRect *own,
                          const GramChunk *chunks, int nchunks, float *part, cudaStream_t s);
@@ -88,6 +90,14 @@ void launch_finish_loss(const double *parts, double *loss, cudaStream_t s);
 // k_tc.cu: tcgen05 / TMEM / TMA implicit-GEMM convolution (BF16 in, FP32 accumulate)
 // Returns cudaSuccess or the error of tensor-map encoding / launch.
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s);
+// Patch rule of the tensor-core convolution that a launch of this shape runs: fixed 16 x 8
+// patches (*fixed, the halo kernel of the 64-channel layers) or any TH x TW with
+// TH * TW <= *rows pixels (128; 256 for the pixels-as-N kernel of 128-channel outputs).
+void conv_tc_patch_rule(int cin, int cout, int taps, int k2, int *rows, bool *fixed);
+// The patch shape within that rule that covers n rectangles h[i] x w[i] with the fewest
+// patches (with fused pooling TW is 8 or 16 and TH * TW = rows).
+void conv_tc_pick_patch(const int *h, const int *w, int n, int rows, bool fixed, bool pool,
+                        int *TH, int *TW);
 bool tc_available();
 void *tc_encode_tiled_fn();   // cuTensorMapEncodeTiled (driver entry point), null if unavailable
 int tc_num_sms();
@@ -124,6 +134,22 @@ void gram_tc_patch(int own_h, int own_w, int *TH, int *TW);
 cudaError_t encode_gram_map(CUtensorMap *m, const void *base, int C, int own_w, int own_h,
                             long long row_stride_px, int TH, int TW);
 cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStream_t s);
+
+// Chunking of a flat [npix][C] feature matrix for the CUDA-core Gram kernels: about 1,216 CTAs
+// over the 64 x 64 block pairs (npairs = nb (nb + 1) / 2, nb = C / 64), chunks of a multiple of
+// 32 pixels, at least 256. nchunks * npairs <= 1,216 whenever npix > 256 * 1216 / npairs.
+inline void gram_flat_plan(long long npix, int C, long long *chunk_len, int *nchunks) {
+  const int nb = C / 64, npairs = nb * (nb + 1) / 2;
+  const long long target = 1216 / npairs > 1 ? 1216 / npairs : 1;
+  long long ch = (npix + target - 1) / target;
+  if (ch < 256) ch = 256;
+  ch = (ch + 31) / 32 * 32;
+  *chunk_len = ch;
+  *nchunks = (int)((npix + ch - 1) / ch);
+}
+
+// context-free error message (returned by nst_last_error(NULL)); defined in nst_api.cu
+void set_last_error_msg(const char *msg);
 
 // k_lbfgs.cu (L-BFGS launchers are declared in nst_lbfgs_dev.h)
 void launch_bicubic(const float *x, int C, int h, int w, float *out, int H, int W,

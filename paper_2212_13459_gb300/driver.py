@@ -80,11 +80,11 @@ def scaled(n, f):
 
 
 def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callback=None,
-               host_history_last=False, **cfg):
+               host_history_last=False, x0=None, **cfg):
     """Algorithm 2: for s = 1..n, downscale (u, v) by 2^(n-s) (area averaging, sizes rounded);
-    x = u at the first scale, else the previous x upscaled by 2 (bicubic); then L-BFGS with
-    localized gradients (history 100 at the first scale, 10 afterwards).
-    tiles_for(H, W) -> (k_h, k_w) picks the block grid of a scale."""
+    x = u at the first scale (or x0, a 3 x h x w image of the first scale's size), else the
+    previous x upscaled by 2 (bicubic); then L-BFGS with localized gradients (history 100 at the
+    first scale, 10 afterwards). tiles_for(H, W) -> (k_h, k_w) picks the block grid of a scale."""
     schedule = schedule or spst_schedule(n_scales)
     x = None
     for s in range(1, n_scales + 1):
@@ -93,7 +93,12 @@ def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callb
         Hv, Wv = scaled(v.shape[1], f), scaled(v.shape[2], f)
         us = u if f == 1 else downscale(u, Hs, Ws)
         vs = v if f == 1 else downscale(v, Hv, Wv)
-        x = us.clone() if x is None else resample(x, Hs, Ws)
+        if x is None:
+            x = (us if x0 is None else x0.to(device=us.device, dtype=torch.float32)).clone()
+            if tuple(x.shape) != tuple(us.shape):
+                raise ValueError("x0 must be 3 x %d x %d (the first scale)" % (Hs, Ws))
+        else:
+            x = resample(x, Hs, Ws)
         kh, kw = tiles_for(Hs, Ws) if tiles_for else (1, 1)
         ctx = native.Context(params_flat, tiles_h=kh, tiles_w=kw, **cfg)
         ctx.style_targets(vs)
@@ -106,15 +111,17 @@ def multiscale(params_flat, u, v, n_scales, schedule=None, tiles_for=None, callb
 
 
 def texture_synthesis(params_flat, v, H, W, n_scales, schedule=None, seed=0, tiles_for=None,
-                      callback=None, **cfg):
+                      callback=None, x0=None, **cfg):
     """Texture synthesis (Section 6.2): the multiscale loop with no content term (lambda_c = 0),
-    starting from white noise at the coarsest scale; the output is H x W."""
-    g = torch.Generator(device=v.device).manual_seed(seed)
+    starting from white noise (uniform in [0, 1]) at the coarsest scale, or from the given x0 of
+    that size; the output is H x W."""
     f = 2 ** (n_scales - 1)
-    noise = torch.rand((3, scaled(H, f), scaled(W, f)), device=v.device, generator=g)
-    # the content image only fixes the sizes (its term has weight 0); noise at every scale
-    u = resample(noise, H, W)
+    if x0 is None:
+        g = torch.Generator(device=v.device).manual_seed(seed)
+        x0 = torch.rand((3, scaled(H, f), scaled(W, f)), device=v.device, generator=g)
+    # the content image only fixes the sizes of the scales (its term has weight 0)
+    u = torch.zeros((3, H, W), device=v.device, dtype=torch.float32)
     cfg = dict(cfg)
     cfg["lambda_c"] = 0.0
     return multiscale(params_flat, u, v, n_scales, schedule=schedule, tiles_for=tiles_for,
-                      callback=callback, **cfg)
+                      callback=callback, x0=x0, **cfg)

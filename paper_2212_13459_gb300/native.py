@@ -305,17 +305,29 @@ def conv3x3(dtype, engine, inp, w, out, bias=None, mode=0, mask=None, in2=None, 
                              _ptr(out), _stream(stream)))
 
 
+def _gram_args(V, G):
+    """Marshalling checks shared by gram() and gram_noalloc(): V a contiguous 2-D float32 or
+    bfloat16 matrix [npix, C] and G a contiguous C x C float64 matrix on the same device."""
+    import torch
+    if V.dim() != 2 or not V.is_contiguous() or V.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("V must be a contiguous 2-D float32 or bfloat16 tensor")
+    C = V.shape[1]
+    if G.dtype != torch.float64 or tuple(G.shape) != (C, C) or not G.is_contiguous():
+        raise ValueError("G must be a contiguous %d x %d float64 tensor" % (C, C))
+    if V.device != G.device or V.device.type != "cuda":
+        raise ValueError("V and G must be on the same CUDA device")
+    return PREC_BF16 if V.dtype == torch.bfloat16 else PREC_FP32
+
+
 def gram(V, G, stream=None):
     """G (C x C float64, device) = V^T V for V [npix, C] (float32 or bfloat16, device)."""
-    import torch
-    dtype = PREC_BF16 if V.dtype == torch.bfloat16 else PREC_FP32
+    dtype = _gram_args(V, G)
     _check(lib().nst_gram(dtype, _ptr(V), V.shape[0], V.shape[1], _ptr(G), _stream(stream)))
 
 
 def gram_noalloc(V, G, stream=None):
     """As gram(), through nst_gram_noalloc: no device allocation by the library (its partial sums
     use a fixed array in the library's device image; calls must not overlap on the GPU)."""
-    import torch
-    dtype = PREC_BF16 if V.dtype == torch.bfloat16 else PREC_FP32
+    dtype = _gram_args(V, G)
     _check(lib().nst_gram_noalloc(dtype, _ptr(V), V.shape[0], V.shape[1], _ptr(G),
                                   _stream(stream)))

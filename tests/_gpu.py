@@ -23,21 +23,26 @@ def seeded(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
     return params, u, v, x
 
 
-# BF16 gradient bound of the full loss: the gradient of the VGG trunk is discontinuous at every
-# ReLU / max-pool decision; with 8-bit mantissas, pooling windows whose top values sit within an
-# ulp flip under any change of rounding or accumulation order. Measured with the oracle alone:
-# rounding only the stored values to bfloat16 moves dE/dx by 0.23 (64x64 and 128x128), and the
-# exact gradient itself moves by 0.175 when x is perturbed by one bfloat16 ulp (4e-3 relative).
-# The pool-free ReLU1_1 term keeps the 2e-2 bound (6.6e-4 measured).
-TOL_BF16_FULL_GRAD = 0.35
+# BF16 gradient bound of the full loss. The gradient of the VGG trunk is discontinuous at every
+# ReLU / max-pool decision, and storing activations in BF16 (8-bit mantissa) perturbs every
+# pre-activation by ~1e-3 relative, which flips the decisions that lie that close to a tie.
+# Measured with the oracle alone (storage="bf16" against the plain FP64 definition): 0.23 at
+# 64x64 and 0.27 at 128x128 for the full loss; 7e-3 for the ReLU1_1 term (no pooling decision on
+# its path), 0.11 / 0.18 / 0.22 / 0.32 for the ReLU2_1 .. ReLU5_1 terms. The GPU's BF16 form is
+# therefore held, case by case, to FLOOR_FACTOR times the deviation that BF16 storage causes in
+# the oracle itself on the same input (never below TOL_BF16): see bf16_grad_bound().
+TOL_BF16_FULL_GRAD = 0.35   # a fixed bound, only where no oracle floor is at hand
+FLOOR_FACTOR = 1.5
 STYLE1_ONLY = (0.2, 0.0, 0.0, 0.0, 0.0)
 
 
 @functools.lru_cache(maxsize=None)
 def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, storage="f64",
                   ws=None, lam=None):
-    """FP64 oracle; storage="bf16"/"f32" rounds where that form of the path stores values, so
-    ReLU masks and pooling argmaxes are decided in the same precision on both sides."""
+    """FP64 oracle (ws a tuple: results are cached by argument). storage="f64" is the plain
+    definition; "f32"/"bf16" round where that form of the path stores values (the FP32 form is
+    compared with "f32", so that its ReLU masks and pooling argmaxes are decided in the same
+    precision on both sides; "bf16" only serves to measure what BF16 storage alone does)."""
     params, u, v, x = seeded(H, W, seed, Hv, Wv, noise, bias_std)
     P = oracle.pack_params(params)
     ws = np.array(W_STYLE if ws is None else ws, np.float64)
@@ -47,6 +52,16 @@ def oracle_result(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, storage
         Gv = oracle.style_grams(P, v)
         E, g, parts, Gx = oracle.loss_grad(P, x, ct, Gv, ws, lam)
     return E, g, parts, Gx, Gv
+
+
+def bf16_grad_bound(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, ws=None, lam=None):
+    """Gradient bound of the BF16 form against the plain FP64 oracle on one problem: the relative
+    deviation of the oracle's own BF16-storage evaluation from the definition (the error that
+    rounding the stored values alone causes), times FLOOR_FACTOR, at least TOL_BF16. Computed
+    from the oracle alone."""
+    g64 = oracle_result(H, W, seed, Hv, Wv, noise, bias_std, "f64", ws, lam)[1]
+    g16 = oracle_result(H, W, seed, Hv, Wv, noise, bias_std, "bf16", ws, lam)[1]
+    return max(TOL_BF16, FLOOR_FACTOR * rel_l2(g16, g64))
 
 
 def run_gpu(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0, x=None, **cfg):

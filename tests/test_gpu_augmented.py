@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_2212_13459_gb300 import native, synth
-from tests._gpu import (LAMBDA_C, STYLE1_ONLY, TOL_BF16, TOL_BF16_FULL_GRAD, TOL_FP32, rel_l2,
+from tests._gpu import (LAMBDA_C, STYLE1_ONLY, TOL_BF16, FLOOR_FACTOR, TOL_FP32, rel_l2,
                         seeded)
 
 pytestmark = pytest.mark.gpu
@@ -67,19 +67,25 @@ def test_augmented_fp32(case):
 
 
 def test_augmented_bf16_tensor_cores():
-    E, g, parts, mv, sv = oracle_aug(128, 128, 1, "bf16", W_STYLE, W_MEAN, W_STD, LAMBDA_C)
+    """Against the plain FP64 definition; the gradient within 1.5 times the deviation that BF16
+    storage alone causes in the oracle on the same problem."""
+    E, g, parts, mv, sv = oracle_aug(128, 128, 1, "f64", W_STYLE, W_MEAN, W_STD, LAMBDA_C)
+    g16 = oracle_aug(128, 128, 1, "bf16", W_STYLE, W_MEAN, W_STD, LAMBDA_C)[1]
+    bound = max(TOL_BF16, FLOOR_FACTOR * rel_l2(g16, g))
     r = gpu_aug(128, 128, 1, W_STYLE, W_MEAN, W_STD, LAMBDA_C, tiles_h=2, tiles_w=2, **TC)
     assert r["status"] == 0
     for s in range(5):
         assert rel_l2(r["mv"][s], mv[s]) <= TOL_BF16 and rel_l2(r["sv"][s], sv[s]) <= TOL_BF16
     assert abs(r["E"] - E) <= TOL_BF16 * abs(E)
-    assert rel_l2(r["g"], g) <= TOL_BF16_FULL_GRAD
+    err = rel_l2(r["g"], g)
+    print("augmented bf16: grad rel err %.3e (bound %.3e)" % (err, bound))
+    assert err <= bound
 
 
 def test_augmented_relu1_1_terms_bf16_strict():
     """Mean and std terms at ReLU1_1 only (no pooling decision on the gradient path)."""
     wm, wsd = (0.5, 0, 0, 0, 0), (0.4, 0, 0, 0, 0)
-    E, g, parts, mv, sv = oracle_aug(96, 96, 3, "bf16", STYLE1_ONLY, wm, wsd, 0.0)
+    E, g, parts, mv, sv = oracle_aug(96, 96, 3, "f64", STYLE1_ONLY, wm, wsd, 0.0)
     r = gpu_aug(96, 96, 3, STYLE1_ONLY, wm, wsd, 0.0, tiles_h=2, tiles_w=2, **TC)
     assert abs(r["E"] - E) <= TOL_BF16 * abs(E)
     assert rel_l2(r["g"], g) <= TOL_BF16

@@ -7,25 +7,28 @@ import pytest
 import torch
 
 from paper_2212_13459_gb300 import driver, native
-from tests._gpu import TOL_BF16_FULL_GRAD, rel_l2, run_gpu
+from tests._gpu import rel_l2, run_gpu
 
 pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("name,cfg,tol,gtol", [
-    ("fp32", dict(precision=native.PREC_FP32), 1e-5, 1e-2),
-    ("bf16", dict(precision=native.PREC_BF16), 2e-3, TOL_BF16_FULL_GRAD)])
+    ("fp32", dict(precision=native.PREC_FP32), 1e-5, 1e-4),
+    ("bf16", dict(precision=native.PREC_BF16), 2e-3, 1e-3)])
 def test_config2_untiled_equals_4x4_blocks(name, cfg, tol, gtol):
-    """Statistics and loss to the accumulation-order level; the gradient within the allowance
-    for pooling / ReLU decisions that the two accumulation orders take differently (FP32: 1e-2,
-    BF16: the decision bound)."""
+    """Statistics and loss to the accumulation-order level. Every owned activation is the same
+    per-pixel sum in the same order whichever block holds it, so the ReLU and pooling decisions
+    agree and only the grouping of the Gram partial sums differs: the gradients agree to that
+    level (measured: 1.2e-6 in FP32, bitwise in BF16, where R_L's rounding absorbs it)."""
     a = run_gpu(512, 512, 1, **cfg)
     b = run_gpu(512, 512, 1, tiles_h=4, tiles_w=4, **cfg)
     assert a["status"] == 0 and b["status"] == 0
     for s in range(5):
         assert rel_l2(b["grams"][s], a["grams"][s]) <= tol, s
     assert abs(b["E"] - a["E"]) <= tol * abs(a["E"])
-    assert rel_l2(b["g"], a["g"]) <= gtol
+    err = rel_l2(b["g"], a["g"])
+    print("config2 %s: untiled vs 4x4 grad rel diff %.3e" % (name, err))
+    assert err <= gtol
 
 
 def test_config2_lbfgs_100_iterations_bf16():

@@ -1,13 +1,16 @@
-"""Full-size parity at the benchmark workload (3024 x 4032, 8 x 8 blocks, margins 80/160).
+"""Full-size parity at the benchmark workloads: 3024 x 4032 with 8 x 8 blocks (scale 3) and
+6048 x 8064 with 16 x 16 blocks (scale 4), margins 80/160.
 
-The oracle cannot evaluate the whole VGG-19 at this size, but the ReLU1_1 Gram term is local
+The oracle cannot evaluate the whole VGG-19 at these sizes, but the ReLU1_1 Gram term is local
 given the global statistics: the oracle forms G^{ReLU1_1}(x) and G^{ReLU1_1}(v) of the whole
 images strip by strip, then Algorithm 1's Step 2 on a 5 x 5 block around each sampled pixel.
-That checks the block plan, the Gram accumulation over 64 blocks, the fused V R term, the
+That checks the block plan, the Gram accumulation over 64 (256) blocks, the fused V R term, the
 backward chain and the inner-part scatter at full size, element by element on the samples
 (block boundaries and image corners included). x is the oracle's own bicubic x2 upsampling of
-the synthetic previous-scale image (nothing here comes from the CUDA path). A second test runs
-the identity x = u = v at 6048 x 8064, 16 x 16 blocks.
+the synthetic previous-scale image (nothing here comes from the CUDA path). The FP32 form is
+compared with the float32-storage oracle, the BF16 form with the plain FP64 definition (on this
+term its error is the BF16 rounding of conv1_1's weights and of the stored values, ~7e-3). A
+further test runs the identity x = u = v at 6048 x 8064.
 """
 import functools
 
@@ -22,12 +25,15 @@ from tests._gpu import TOL_BF16, TOL_FP32, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-H, W, HV, WV, SEED, K = 3024, 4032, 2113, 2660, 3, 8
+# (H, W, style Hv, Wv, seed, blocks per side)
+WORKLOADS = {"scale3": (3024, 4032, 2113, 2660, 3, 8),
+             "scale4": (6048, 8064, 4226, 5319, 4, 16)}
 WS = np.array([0.2, 0.0, 0.0, 0.0, 0.0])
 
 
-@functools.lru_cache(maxsize=1)
-def images():
+@functools.lru_cache(maxsize=2)
+def images(wl):
+    H, W, HV, WV, SEED, K = WORKLOADS[wl]
     small = synth.scale2_result(H // 2, W // 2, SEED)
     x = bicubic.upsample(small.astype(np.float64), H, W).astype(np.float32)
     v = synth.stroke_style(HV, WV, SEED)
@@ -35,19 +41,21 @@ def images():
     return np.ascontiguousarray(x), v, u
 
 
-def sample_points():
+def sample_points(wl):
+    H, W, HV, WV, SEED, K = WORKLOADS[wl]
     rng = np.random.default_rng(17)
     pts = [(int(rng.integers(0, H)), int(rng.integers(0, W))) for _ in range(40)]
     plan = native.tile_plan(H, W, K, K, 160)
-    for r in plan[::9]:                       # pixels straddling inner block boundaries
+    for r in plan[::(K + 1)]:                 # pixels straddling inner block boundaries
         pts += [(int(r[0]), int(r[2])), (int(r[0]) - 1, int(r[2]) - 1), (int(r[1]) - 1, int(r[3]) - 1)]
     pts += [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0)]
     return [(min(max(p, 0), H - 1), min(max(q, 0), W - 1)) for p, q in pts]
 
 
-@functools.lru_cache(maxsize=None)
-def oracle_samples(storage):
-    x, v, u = images()
+@functools.lru_cache(maxsize=4)
+def oracle_samples(wl, storage):
+    H, W, HV, WV, SEED, K = WORKLOADS[wl]
+    x, v, u = images(wl)
     P = oracle.pack_params(synth.vgg19_params(SEED))
     with oracle.storage(storage):
         G1 = oracle.relu11_gram(P, x)
@@ -55,7 +63,7 @@ def oracle_samples(storage):
         zeros = [np.zeros((c, c)) for c in oracle.STYLE_CHANNELS]
         npg = [H * W, 1, 1, 1, 1]
         vals = []
-        for (py, px) in sample_points():
+        for (py, px) in sample_points(wl):
             y0, y1, x0, x1 = max(0, py - 2), min(H, py + 3), max(0, px - 2), min(W, px + 3)
             d = oracle.block_style_grad(P, x[:, y0:y1, x0:x1], [G1] + zeros[1:],
                                         [Gv1] + zeros[1:], npg, WS)
@@ -64,8 +72,9 @@ def oracle_samples(storage):
     return np.array(vals), E, G1, Gv1
 
 
-def gpu_run(**cfg):
-    x, v, u = images()
+def gpu_run(wl, **cfg):
+    H, W, HV, WV, SEED, K = WORKLOADS[wl]
+    x, v, u = images(wl)
     ctx = native.Context(synth.flat_params(synth.vgg19_params(SEED)), tiles_h=K, tiles_w=K,
                          w_style=WS, lambda_c=0.0, **cfg)
     ctx.style_targets(torch.from_numpy(v).cuda())
@@ -78,22 +87,26 @@ def gpu_run(**cfg):
     parts, grams = ctx.stats()
     sg = ctx.style_grams()
     gs = g.cpu().numpy()
-    vals = np.array([gs[:, py, px] for (py, px) in sample_points()], np.float64)
+    vals = np.array([gs[:, py, px] for (py, px) in sample_points(wl)], np.float64)
     st = ctx.sync_status()
     ctx.close()
     return vals, loss.item(), grams[0], sg[0], st
 
 
+@pytest.mark.parametrize("wl", [pytest.param("scale3"),
+                                pytest.param("scale4", marks=pytest.mark.slow)])
 @pytest.mark.parametrize("name,cfg,storage,tol", [
     ("fp32", dict(precision=native.PREC_FP32, conv_engine=native.CONV_SIMT), "f32", TOL_FP32),
-    ("bf16-tc", dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC), "bf16", TOL_BF16)])
-def test_relu1_1_term_full_size_sampled(name, cfg, storage, tol):
-    ref, E, G1, Gv1 = oracle_samples(storage)
-    vals, loss, g1, gv1, st = gpu_run(**cfg)
+    ("bf16-tc", dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC), "f64", TOL_BF16)])
+def test_relu1_1_term_full_size_sampled(wl, name, cfg, storage, tol):
+    ref, E, G1, Gv1 = oracle_samples(wl, storage)
+    vals, loss, g1, gv1, st = gpu_run(wl, **cfg)
     assert st == 0
     assert rel_l2(g1, G1) <= tol and rel_l2(gv1, Gv1) <= tol
     assert abs(loss - E) <= tol * abs(E)
-    assert rel_l2(vals, ref) <= tol, rel_l2(vals, ref)
+    err = rel_l2(vals, ref)
+    print("%s %s: ReLU1_1-term gradient at %d samples rel err %.3e" % (wl, name, len(vals), err))
+    assert err <= tol, err
 
 
 def test_identity_scale4_exact_zero():

@@ -1,9 +1,10 @@
 """GPU parity of the localized loss and image gradient (Algorithm 1) against the FP64 oracle.
 
 Inputs are seeded synthetic images; every case compares libnst's loss, content term, the five
-Gram matrices G^L(x) and G^L(v), and dE/dx element by element with the untiled oracle evaluated
-in the same storage precision as the form under test (ReLU masks and pooling argmaxes are
-floating-point decisions, so both sides take them in that precision).
+Gram matrices G^L(x) and G^L(v), and dE/dx element by element with the untiled oracle: for the
+FP32 form the oracle with float32 storage (ReLU masks and pooling argmaxes are floating-point
+decisions, so both sides take them in that precision), for the BF16 forms the plain FP64
+definition.
 
 Tolerances (relative): FP32 form 1e-5; BF16 forms 2e-2. The gradient is discontinuous where a
 ReLU input or a pooling window's top two values meet; a decision whose value lies inside the
@@ -13,8 +14,9 @@ large enough to hold such decisions allow 1e-2 on the FP32 gradient; the loss an
 matrices are continuous and keep the strict bound everywhere.
 
 BF16: the loss, the content term and all Gram matrices keep 2e-2. The gradient keeps 2e-2 for
-the ReLU1_1 style term (no pooling before it); the full loss's gradient is held to the BF16
-decision bound TOL_BF16_FULL_GRAD (see tests/_gpu.py for its derivation).
+the ReLU1_1 style term (no pooling before it); the full loss's gradient is held to 1.5 times the
+deviation that BF16 storage alone causes in the oracle on the same problem (bf16_grad_bound in
+tests/_gpu.py).
 """
 import numpy as np
 import pytest
@@ -22,14 +24,14 @@ import torch
 
 import oracle as oracle_mod
 from paper_2212_13459_gb300 import native, synth
-from tests._gpu import (LAMBDA_C, STYLE1_ONLY, TOL_BF16, TOL_BF16_FULL_GRAD, TOL_FP32, W_STYLE,
+from tests._gpu import (LAMBDA_C, STYLE1_ONLY, TOL_BF16, TOL_FP32, W_STYLE, bf16_grad_bound,
                         oracle_result, rel_l2, run_gpu, seeded)
 
 pytestmark = pytest.mark.gpu
 
 FP32 = dict(precision=native.PREC_FP32, conv_engine=native.CONV_SIMT)
 BF16_SIMT = dict(precision=native.PREC_BF16, conv_engine=native.CONV_SIMT)
-ENGINES = [("fp32", FP32, "f32", TOL_FP32), ("bf16-simt", BF16_SIMT, "bf16", TOL_BF16)]
+ENGINES = [("fp32", FP32, "f32", TOL_FP32), ("bf16-simt", BF16_SIMT, "f64", TOL_BF16)]
 FLIP_ALLOWANCE = 1e-2
 
 # name: (H, W, seed, Hv, Wv, bias_std, cfg, fp32 gradient flip allowance)
@@ -65,7 +67,7 @@ def test_path_parity(case, name, cfg, storage, tol):
     if name == "fp32":
         grad_tol = FLIP_ALLOWANCE if flips else None
     else:
-        grad_tol = TOL_BF16_FULL_GRAD
+        grad_tol = bf16_grad_bound(H, W, seed, Hv, Wv, bias_std=bias)
     compare(res, ref, tol, grad_tol)
 
 
@@ -87,15 +89,15 @@ def test_path_parity_relu1_1_term(case, name, cfg, storage, tol):
 
 
 def test_bf16_against_exact_definition():
-    """The BF16 form against the plain FP64 oracle (no storage rounding on the oracle side):
-    continuous outputs within 2e-2, the gradient within the BF16 decision bound."""
+    """The BF16 CUDA-core form against the plain FP64 oracle: continuous outputs within 2e-2,
+    the gradient within 1.5 times the oracle's own BF16-storage deviation."""
     ref = oracle_result(128, 128, 1)
     res = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, **BF16_SIMT)
     E, g, parts, Gx, Gv = ref
     for s in range(5):
         assert rel_l2(res["grams"][s], Gx[s]) <= TOL_BF16
     assert abs(res["E"] - E) <= TOL_BF16 * abs(E)
-    assert rel_l2(res["g"], g) <= TOL_BF16_FULL_GRAD
+    assert rel_l2(res["g"], g) <= bf16_grad_bound(128, 128, 1)
 
 
 @pytest.mark.parametrize("name,cfg,storage,tol", ENGINES)
@@ -157,7 +159,9 @@ def test_call_order_and_shape_errors():
 def test_resident_and_two_pass_agree(name, cfg, two_pass, expect):
     """All blocks in one batch (one forward pass supplies both steps) against Algorithm 1 as
     printed (Step-1 pass with margin 80, forward recomputed in Step 2), with one block per batch
-    or with every block in one batch."""
+    or with every block in one batch. Both schedules take every ReLU and pooling decision on the
+    same values (each owned activation is the same per-pixel sum in the same order), and only
+    the grouping of the Gram partial sums differs, so even the BF16 gradient agrees closely."""
     a = run_gpu(96, 128, 4, tiles_h=2, tiles_w=2, **cfg)
     b = run_gpu(96, 128, 4, tiles_h=2, tiles_w=2, **two_pass, **cfg)
     assert a["pass_info"] == (1, True) and b["pass_info"] == expect
@@ -165,11 +169,14 @@ def test_resident_and_two_pass_agree(name, cfg, two_pass, expect):
     for s in range(5):
         assert rel_l2(a["grams"][s], b["grams"][s]) <= (1e-6 if name == "fp32" else 2e-3)
     assert abs(a["E"] - b["E"]) <= (1e-6 if name == "fp32" else 2e-3) * abs(b["E"])
-    assert rel_l2(a["g"], b["g"]) <= (1e-5 if name == "fp32" else TOL_BF16_FULL_GRAD)
+    err = rel_l2(a["g"], b["g"])
+    print("%s %s: grad rel diff %.3e" % (name, two_pass, err))
+    assert err <= 1e-5   # measured: 0 (bitwise equal) in both forms
 
 
-# measured 0.040 (CUDA-core form) and 0.046 (tensor-core form); a one-pixel misroute moves the
-# interior gradient by 1.17-1.27 of its norm (oracle alone, shifting the through-pool part)
+# CUDA-core BF16 engine against the bfloat16-storage oracle (both pool the stored values): 0.040
+# measured. A one-pixel misroute moves the interior gradient by 1.17-1.27 of its norm (oracle
+# alone, shifting the through-pool part).
 TIE_TOL = 0.1
 
 
@@ -178,29 +185,40 @@ TIE_TOL = 0.1
 def test_pool_ties_route_to_first_max(engine, tiles):
     """Exact ties in the pooling windows. With a constant image every interior conv1_2 output
     is computed by the same arithmetic at every pixel, so each interior 2 x 2 window holds four
-    bitwise-equal values on both sides (checked on the oracle). The oracle sends a tied
-    window's gradient to the first maximum in row-major order; the tensor-core form routes by
-    the window positions its fused pooling recorded, the CUDA-core form by the stored
-    activation. Sending it to any other pixel of the window moves the part of dE/dx that
-    passes through pool1 by one pixel (1.17-1.27 of the interior gradient's norm), so the
-    bound here is far tighter than the general BF16 gradient bound: the remaining decisions
-    (ReLU gates, border windows) are few."""
+    bitwise-equal values, in FP64 and in any storage precision (checked on the oracle). The
+    oracle sends a tied window's gradient to the first maximum in row-major order; the
+    tensor-core form routes by the window positions its fused pooling recorded (decided on the
+    FP32 values), the CUDA-core form by the stored activation. Sending it to any other pixel of
+    the window moves the part of dE/dx that passes through pool1 by one pixel (1.17-1.27 of the
+    interior gradient's norm), far above either bound. The tensor-core form is compared with the
+    plain definition within 1.5 times the oracle's own BF16-storage deviation on this input
+    (0.16, the border windows' and deeper layers' decisions); the CUDA-core form, which pools the
+    stored BF16 values like the storage-mode oracle, with that oracle within TIE_TOL."""
     H = W = 64
     seed = 0
     params, u, v, _ = seeded(H, W, seed)
     x = np.full((3, H, W), 0.5, np.float32)
     P = oracle_mod.pack_params(params)
-    with oracle_mod.storage("bf16"):
-        a = np.asarray(oracle_mod.features(P, x, 1))[:, 2:62, 2:62]
-        assert np.all((a[:, 0::2, 0::2] == a[:, 0::2, 1::2]) & (a[:, 0::2, 0::2] == a[:, 1::2, 0::2])
-                      & (a[:, 0::2, 0::2] == a[:, 1::2, 1::2]))
-        ct = oracle_mod.content_target(P, u)
-        Gv = oracle_mod.style_grams(P, v)
-        E, g, parts, Gx = oracle_mod.loss_grad(P, x, ct, Gv, np.array(W_STYLE, np.float64),
-                                               LAMBDA_C)
+    ref = {}
+    for storage in ("f64", "bf16"):
+        with oracle_mod.storage(storage):
+            a = np.asarray(oracle_mod.features(P, x, 1))[:, 2:62, 2:62]
+            assert np.all((a[:, 0::2, 0::2] == a[:, 0::2, 1::2])
+                          & (a[:, 0::2, 0::2] == a[:, 1::2, 0::2])
+                          & (a[:, 0::2, 0::2] == a[:, 1::2, 1::2]))
+            ct = oracle_mod.content_target(P, u)
+            Gv = oracle_mod.style_grams(P, v)
+            ref[storage] = oracle_mod.loss_grad(P, x, ct, Gv, np.array(W_STYLE, np.float64),
+                                                LAMBDA_C)
+    if engine == native.CONV_TC:
+        E, g = ref["f64"][0], ref["f64"][1]
+        tol = max(TIE_TOL, 1.5 * rel_l2(ref["bf16"][1], g))
+    else:
+        E, g = ref["bf16"][0], ref["bf16"][1]
+        tol = TIE_TOL
     res = run_gpu(H, W, seed, x=x, precision=native.PREC_BF16, conv_engine=engine, **tiles)
     assert res["status"] == 0
     assert abs(res["E"] - E) <= TOL_BF16 * abs(E)
     err = rel_l2(res["g"], np.asarray(g))
-    print("tie case", engine, tiles, "grad rel err", err)
-    assert err <= TIE_TOL, err
+    print("tie case", engine, tiles, "grad rel err %.3e (bound %.3e)" % (err, tol))
+    assert err <= tol, (err, tol)

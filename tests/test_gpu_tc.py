@@ -4,7 +4,8 @@ Unit level: one layer through nst_conv3x3 against PyTorch's own FP32 conv2d of t
 BF16-rounded inputs (forward with bias/ReLU/valid-region zeroing, backward gating by a mask, the
 fused style-gradient K extension V R, and that extension alone), for the channel counts of the
 VGG-19 trunk and ragged spatial sizes. Path level: the full Algorithm 1 evaluation with the
-tensor-core engine against the FP64 oracle (BF16 tolerance 2e-2).
+tensor-core engine, in each schedule, against the plain FP64 oracle (Grams, loss and content
+term within 2e-2; the gradient within a bound derived from the oracle alone, see tests/_gpu.py).
 """
 import numpy as np
 import pytest
@@ -12,8 +13,8 @@ import torch
 import torch.nn.functional as F
 
 from paper_2212_13459_gb300 import native
-from tests._gpu import (STYLE1_ONLY, TOL_BF16, TOL_BF16_FULL_GRAD, oracle_result, rel_l2,
-                        run_gpu)
+from tests._gpu import (STYLE1_ONLY, TOL_BF16, TOL_BF16_FULL_GRAD, bf16_grad_bound,
+                        oracle_result, rel_l2, run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -131,46 +132,80 @@ def test_single_layer_fp32_simt():
     assert ((out - ref).norm() / ref.norm()).item() <= 1e-5
 
 
-def _cmp(res, ref, tol, grad_tol=TOL_BF16_FULL_GRAD):
+def _cmp(res, ref, tol, grad_tol):
     E, g, parts, Gx, Gv = ref
     assert res["status"] == 0
     for s in range(5):
         assert rel_l2(res["style_grams"][s], Gv[s]) <= tol, s
         assert rel_l2(res["grams"][s], Gx[s]) <= tol, s
     assert abs(res["E"] - E) <= tol * abs(E)
-    assert rel_l2(res["g"], g) <= grad_tol, rel_l2(res["g"], g)
+    assert abs(res["parts"][5] - parts[5]) <= tol * abs(parts[5]) + 1e-12
+    err = rel_l2(res["g"], g)
+    assert err <= grad_tol, (err, grad_tol)
+    return err
 
 
 TC = dict(precision=native.PREC_BF16, conv_engine=native.CONV_TC)
+# the schedules of Algorithm 1 the library runs: all blocks resident (one forward pass), the
+# printed two-pass schedule (Step-1 pass with margin 80, forward recomputed in Step 2), and one
+# block per batch
+SCHEDULES = {"resident": dict(), "two_pass": dict(schedule=native.SCHED_TWO_PASS),
+             "one_block_per_batch": dict(max_batch_tiles=1)}
+# (H, W, seed, Hv, Wv, bias_std, tiles)
+PATH_CASES = {
+    "config1_64x64_2x2": (64, 64, 0, None, None, 0.0, dict(tiles_h=2, tiles_w=2)),
+    "untiled_128": (128, 128, 1, None, None, 0.0, dict()),
+    "ragged_100x76_bias_2x3": (100, 76, 2, 90, 111, 0.01, dict(tiles_h=2, tiles_w=3)),
+    "margins_cut_96x480_1x3": (96, 480, 3, None, None, 0.0, dict(tiles_h=1, tiles_w=3)),
+}
 
 
-# the oracle evaluated with bfloat16 storage (decisions in the form's precision)
-def test_path_tc_config1():
-    _cmp(run_gpu(64, 64, 0, tiles_h=2, tiles_w=2, **TC),
-         oracle_result(64, 64, 0, storage="bf16"), TOL_BF16)
+@pytest.mark.parametrize("sched", list(SCHEDULES))
+@pytest.mark.parametrize("case", list(PATH_CASES))
+def test_path_tc_against_definition(case, sched):
+    """The tensor-core BF16 form against the plain FP64 oracle (no rounding on the oracle side):
+    G^L(x), G^L(v), the loss and the content term within 2e-2; dE/dx within FLOOR_FACTOR times
+    the deviation BF16 storage alone causes in the oracle on the same problem."""
+    H, W, seed, Hv, Wv, bias, tiles = PATH_CASES[case]
+    if sched == "one_block_per_batch" and not tiles:
+        pytest.skip("untiled: one block")
+    res = run_gpu(H, W, seed, Hv, Wv, bias_std=bias, **tiles, **SCHEDULES[sched], **TC)
+    bound = bf16_grad_bound(H, W, seed, Hv, Wv, bias_std=bias)
+    err = _cmp(res, oracle_result(H, W, seed, Hv, Wv, bias_std=bias), TOL_BF16, bound)
+    print("%s %s: grad rel err %.3e (bound %.3e)" % (case, sched, err, bound))
 
 
-def test_path_tc_untiled_128():
-    _cmp(run_gpu(128, 128, 1, **TC), oracle_result(128, 128, 1, storage="bf16"), TOL_BF16)
-
-
-def test_path_tc_ragged_bias():
-    _cmp(run_gpu(100, 76, 2, Hv=90, Wv=111, bias_std=0.01, tiles_h=2, tiles_w=3, **TC),
-         oracle_result(100, 76, 2, Hv=90, Wv=111, bias_std=0.01, storage="bf16"), TOL_BF16)
-
-
-def test_path_tc_margins_cut_blocks():
-    _cmp(run_gpu(96, 480, 3, tiles_h=1, tiles_w=3, **TC),
-         oracle_result(96, 480, 3, storage="bf16"), TOL_BF16)
-
-
+@pytest.mark.parametrize("sched", ["resident", "two_pass"])
 @pytest.mark.parametrize("case", [(64, 64, 0, 2), (128, 128, 1, 1), (96, 480, 3, 3)])
-def test_path_tc_relu1_1_term_strict(case):
-    """ReLU1_1 Gram term only (no pooling decision on the gradient path): 2e-2 on dE/dx."""
+def test_path_tc_relu1_1_term_strict(case, sched):
+    """ReLU1_1 Gram term only (no pooling decision on the gradient path): 2e-2 on dE/dx against
+    the plain FP64 definition."""
     H, W, seed, tw = case
-    _cmp(run_gpu(H, W, seed, tiles_h=1, tiles_w=tw, w_style=STYLE1_ONLY, lambda_c=0.0, **TC),
-         oracle_result(H, W, seed, storage="bf16", ws=STYLE1_ONLY, lam=0.0), TOL_BF16,
-         grad_tol=TOL_BF16)
+    _cmp(run_gpu(H, W, seed, tiles_h=1, tiles_w=tw, w_style=STYLE1_ONLY, lambda_c=0.0,
+                 **SCHEDULES[sched], **TC),
+         oracle_result(H, W, seed, ws=STYLE1_ONLY, lam=0.0), TOL_BF16, TOL_BF16)
+
+
+LAYER_TERMS = {"relu1_1": ((0.2, 0, 0, 0, 0), 0.0), "relu2_1": ((0, 0.2, 0, 0, 0), 0.0),
+               "relu3_1": ((0, 0, 0.2, 0, 0), 0.0), "relu4_1": ((0, 0, 0, 0.2, 0), 0.0),
+               "relu5_1": ((0, 0, 0, 0, 0.2), 0.0), "content": ((0, 0, 0, 0, 0), 1e-3)}
+
+
+@pytest.mark.parametrize("term", list(LAYER_TERMS))
+def test_path_tc_gradient_by_layer(term):
+    """Where the BF16 gradient error arises: one loss term at a time (a single style layer, or
+    the content term) at 128 x 128 with 2 x 2 blocks, against the plain FP64 definition. Each
+    term's bound is FLOOR_FACTOR times the oracle's own BF16-storage deviation for that term;
+    the measured errors are printed."""
+    ws, lam = LAYER_TERMS[term]
+    res = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, w_style=ws, lambda_c=lam, **TC)
+    ref = oracle_result(128, 128, 1, ws=ws, lam=lam)
+    bound = bf16_grad_bound(128, 128, 1, ws=ws, lam=lam)
+    err = rel_l2(res["g"], ref[1])
+    print("term %s: grad rel err %.3e (bound %.3e)" % (term, err, bound))
+    assert res["status"] == 0
+    assert abs(res["E"] - ref[0]) <= TOL_BF16 * abs(ref[0])
+    assert err <= bound, (err, bound)
 
 
 def test_path_tc_matches_simt_bf16():
@@ -178,7 +213,9 @@ def test_path_tc_matches_simt_bf16():
     a = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, **TC)
     b = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, precision=native.PREC_BF16,
                 conv_engine=native.CONV_SIMT)
-    assert rel_l2(a["g"], b["g"]) <= TOL_BF16_FULL_GRAD
+    err = rel_l2(a["g"], b["g"])
+    print("tcgen05 vs CUDA-core BF16: grad rel diff %.3e" % err)
+    assert err <= TOL_BF16_FULL_GRAD
     assert abs(a["E"] - b["E"]) <= 1e-3 * abs(b["E"])
     a1 = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, w_style=STYLE1_ONLY, lambda_c=0.0, **TC)
     b1 = run_gpu(128, 128, 1, tiles_h=2, tiles_w=2, w_style=STYLE1_ONLY, lambda_c=0.0,

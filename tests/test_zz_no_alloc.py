@@ -1,8 +1,10 @@
 """nst_gram_noalloc: the Gram statistics for callers that may not allocate device memory.
 
 Its result must equal that of the allocating entry point nst_gram on the same input, call after
-call: the library-resident scratch array keeps the previous call's contents, so two consecutive
-calls with different inputs are checked. Kept in a file of its own that runs last.
+call: the library-resident scratch array keeps the previous call's contents, so consecutive
+calls with different inputs are checked. Both entries use the same kernels and chunk plan, so
+the two results are bitwise equal as well as within the Gram tests' tolerance. Kept in a file of
+its own that runs last.
 """
 import pytest
 import torch
@@ -28,6 +30,7 @@ def _check_pair(V):
     native.gram_noalloc(V, out)
     torch.cuda.synchronize()
     assert ((out - ref).norm() / ref.norm()).item() <= TOL
+    assert torch.equal(out, ref)
     exact = V.double().T @ V.double()
     assert ((out - exact).norm() / exact.norm()).item() <= TOL
 
@@ -49,3 +52,11 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(native.NSTError) as e:
         native.gram_noalloc(V, G)
     assert e.value.code == native.NST_ERR_SHAPE
+    assert "scratch" in str(e.value)
+    # a channel count that is not a multiple of 64 is an argument error, as for nst_gram
+    V = torch.rand(100, 96, device="cuda")
+    G = torch.zeros((96, 96), dtype=torch.float64, device="cuda")
+    for fn in (native.gram, native.gram_noalloc):
+        with pytest.raises(native.NSTError) as e:
+            fn(V, G)
+        assert e.value.code == native.NST_ERR_INVALID_ARG

@@ -98,11 +98,14 @@ __host__ __device__ constexpr uint32_t fwd_tap_off(int tap) {   // byte offset o
   return (uint32_t)(((tap / 3) * kFwdBoxW + tap % 3) * 16);
 }
 
+// patches: optional list of 16 x 8 output patches {block, y0, x0, 0} (each block's needed
+// rectangle); without it every patch of the buffer, tiles_x x tiles_y per block
 __global__ void __launch_bounds__(kFwdThreads, 2)
     conv11_fwd_tc_kernel(const __grid_constant__ CUtensorMap tmX,
                          const __grid_constant__ CUtensorMap tmO, const float *__restrict__ w11,
                          const float *__restrict__ bias, const BlockGeom *__restrict__ geom,
-                         int B, int Hb, int Wb, int tiles_x, int tiles_y, unsigned *err) {
+                         int B, int Hb, int Wb, int tiles_x, int tiles_y,
+                         const int4 *__restrict__ patches, int npatches, unsigned *err) {
   constexpr uint32_t IDESC = idesc_bf16_m128(64);
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kFwdStages], empty_bar[kFwdStages];
@@ -117,7 +120,19 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
   const uint32_t b_base = smem_base, a_base = smem_base + kFwdB;
   const uint32_t o_off = kFwdB + kFwdStages * kFwdStage;   // output staging tiles
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = B * tiles_x * tiles_y;
+  const int ntiles = patches ? npatches : B * tiles_x * tiles_y;
+  auto origin = [&](int t, int &b, int &y0, int &x0) {
+    if (patches) {
+      const int4 q = __ldg(patches + t);
+      b = q.x;
+      y0 = q.y;
+      x0 = q.z;
+    } else {
+      b = t / (tiles_x * tiles_y);
+      y0 = ((t / tiles_x) % tiles_y) * kFwdTH;
+      x0 = (t % tiles_x) * kFwdTW;
+    }
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kFwdStages; s++) {
@@ -169,11 +184,12 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
         const int stage = it % kFwdStages;
         const uint32_t phase = (uint32_t)(it / kFwdStages) & 1u;
-        const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
+        int b, oy, ox;
+        origin(t, b, oy, ox);
         if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, &abort_flag, err)) break;
         const uint32_t fb = smem_u32(&full_bar[stage]);
         mbar_expect_tx(fb, kFwdBoxBytes);
-        tma_load_4d(a_base + stage * kFwdStage, &tmX, fb, 0, tx * kFwdTW - 1, ty * kFwdTH - 1, b);
+        tma_load_4d(a_base + stage * kFwdStage, &tmX, fb, 0, ox - 1, oy - 1, b);
       }
     }
   } else if (warp == 1) {
@@ -227,8 +243,9 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       tmem_ld32(tb + 32, v + 32);
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
-      const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
-      const int y = ty * kFwdTH + row / kFwdTW, x = tx * kFwdTW + row % kFwdTW;
+      int b, oy, ox;
+      origin(t, b, oy, ox);
+      const int y = oy + row / kFwdTW, x = ox + row % kFwdTW;
       const BlockGeom g = geom[b];
       const bool valid = y < g.eh && x < g.ew;
       uint8_t *orow = smem_gen + o_off + (size_t)(it % kFwdOutBufs) * kFwdOut + (size_t)row * 128;
@@ -247,8 +264,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       fence_proxy_async_smem();
       named_bar_sync(1, 128);
       if (et == 0) {
-        tma_store_4d(&tmO, smem_base + o_off + (uint32_t)(it % kFwdOutBufs) * kFwdOut, 0, tx * kFwdTW,
-                     ty * kFwdTH, b);
+        tma_store_4d(&tmO, smem_base + o_off + (uint32_t)(it % kFwdOutBufs) * kFwdOut, 0, ox, oy,
+                     b);
         bulk_commit();
         bulk_wait_read_3();   // the tile written next (it + 1) was stored at it + 1 - 4
       }
@@ -460,8 +477,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w11,
                                  const float *bias, const BlockGeom *geom, int B, int Hb, int Wb,
-                                 void *stage_buf, __nv_bfloat16 *out, unsigned *err,
-                                 cudaStream_t s) {
+                                 void *stage_buf, __nv_bfloat16 *out, const int4 *patches,
+                                 int npatches, unsigned *err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(conv11_fwd_tc_kernel,
@@ -497,10 +514,12 @@ cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w1
           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const int tiles_x = (Wb + kFwdTW - 1) / kFwdTW, tiles_y = (Hb + kFwdTH - 1) / kFwdTH;
-  const long long ntiles = (long long)B * tiles_x * tiles_y;
+  const long long ntiles = patches ? npatches : (long long)B * tiles_x * tiles_y;
+  if (ntiles <= 0) return cudaSuccess;
   const int grid = (int)std::min<long long>(ntiles, 2LL * tc_num_sms());
   conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(m, mo, w11, bias, geom, B, Hb, Wb,
-                                                           tiles_x, tiles_y, err);
+                                                           tiles_x, tiles_y, patches,
+                                                           (int)ntiles, err);
   return cudaGetLastError();
 }
 

@@ -531,6 +531,19 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
     return pl;
   };
   for (Batch &bt : p.batches) {
+    for (int k = 0; k < kFwdKinds; k++) {
+      // conv1_1 (its own kernel, 16 x 8 patches)
+      PatchList &c11 = bt.fwd[k][0];
+      c11 = PatchList{(int)patches.size(), 0, 16, 8};
+      for (int j = 0; j < bt.B; j++) {
+        const Tile &t = p.tiles[bt.t0 + j];
+        const Iv ry = local_rect(ny[bt.t0 + j].F[k][0], t.ey0, t.ey1 - t.ey0, p.Hb, false);
+        const Iv rx = local_rect(nx[bt.t0 + j].F[k][0], t.ex0, t.ex1 - t.ex0, p.Wb, false);
+        for (int y = ry.a; y < ry.b; y += 16)
+          for (int x = rx.a; x < rx.b; x += 8) patches.push_back(make_int4(j, y, x, 0));
+      }
+      c11.n = (int)patches.size() - c11.off;
+    }
     for (int k = 0; k < kFwdKinds; k++)
       for (int l = 1; l < kNConv; l++)
         bt.fwd[k][l] = add_list(bt, kLevel[l], kCin[l], kCout[l], 9, 0, kPoolAfter[l],
@@ -680,9 +693,11 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
     ctx->launches += ctx->use_tc ? 2 : 1;   // tensor-core form: staging + convolution
     if (ctx->use_tc) {
       // the staged BF16-pair image goes to the (not yet used) second gradient buffer
+      const PatchList &pl = bt.fwd[last_conv == kContentConv ? kFwdContent
+                                  : (for_backward ? kFwdStep2 : kFwdStats)][0];
       cudaError_t e = launch_conv11_fwd_tc(img, p.H, p.W, ctx->d_w11, ctx->d_bias[0], geom, bt.B,
                                            p.Hb, p.Wb, ws.g[1], (__nv_bfloat16 *)ws.act[0],
-                                           ctx->d_err, s);
+                                           p.d_patches + pl.off, pl.n, ctx->d_err, s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "conv1_1 tensor-core forward launch");
     } else {
       launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);

@@ -107,12 +107,14 @@ cudaError_t launch_timeout_check(long long limit_cycles, unsigned *err, cudaStre
 // k_c11_tc.cu: conv1_1 on the tensor cores (BF16 storage). Forward: out[b][y][x][64] =
 // relu(bias + conv1_1(block image)) inside each block's valid extent, zero elsewhere; w11 is
 // [64][3][3][3] FP32 holding BF16 values; stage_buf (16 bytes per buffer pixel, 16-byte aligned)
-// receives the staged block images. Input gradient: grad[ci][ey0 + y][ex0 + x] for the owned
-// (inner) pixels of every block, from the gated ReLU1_1 gradient g [B][Hb][Wb][64].
+// receives the staged block images; patches (optional, npatches 16 x 8 output patches
+// {block, y0, x0, 0}) restricts the convolution to them. Input gradient:
+// grad[ci][ey0 + y][ex0 + x] for the owned (inner) pixels of every block, from the gated
+// ReLU1_1 gradient g [B][Hb][Wb][64].
 cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w11,
                                  const float *bias, const BlockGeom *geom, int B, int Hb, int Wb,
-                                 void *stage_buf, __nv_bfloat16 *out, unsigned *err,
-                                 cudaStream_t s);
+                                 void *stage_buf, __nv_bfloat16 *out, const int4 *patches,
+                                 int npatches, unsigned *err, cudaStream_t s);
 cudaError_t launch_conv11_dgrad_tc(const __nv_bfloat16 *g, const float *w11,
                                    const BlockGeom *geom, const OwnRect *inner, int B, int Hb,
                                    int Wb, int max_inner_h, int max_inner_w, float *grad, int H,

@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
 // Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials. A CTA takes 32
 // consecutive elements (one per lane, coalesced reads); its 8 warps split the runs (warp w sums
 // runs w, w + 8, ... in order) and the 8 partial sums are added in warp order (deterministic).
+// A warp issues the loads of up to 8 of its runs before adding them (in run order), so the
+// loads are in flight together instead of one after another.
 __global__ void __launch_bounds__(256) gram_tc_reduce_kernel(const float *__restrict__ part,
                                                              int nruns, int C, int N, int nI,
                                                              int nJ, double *__restrict__ Gacc) {
@@ -145,7 +147,17 @@ __global__ void __launch_bounds__(256) gram_tc_reduce_kernel(const float *__rest
       const int i = (int)(e / C), j = (int)(e % C);
       const int tile = (i / 128) * nJ + j / N;
       const size_t off = ((size_t)tile * 128 + (i % 128)) * N + (j % N);
-      for (int r = warp; r < nruns; r += 8) s += (double)part[(size_t)r * stride + off];
+      for (int r0 = warp; r0 < nruns; r0 += 64) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          const int r = r0 + 8 * u;
+          v[u] = r < nruns ? __ldg(part + (size_t)r * stride + off) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          if (r0 + 8 * u < nruns) s += (double)v[u];
+      }
     }
     red[warp][lane] = s;
     __syncthreads();

@@ -923,6 +923,181 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---- pixels-as-N halo variant for 64 -> 128 channels ------------------------------------------------
+// conv2_1's forward: M = the 128 output channels (A = one tap's 128 x 64 weight tile, streamed
+// from L2 tap by tap), N = the 256 pixels of a 32 x 8 output patch (B = ONE 34 x 10 activation
+// box per tile; the nine taps are nine descriptors into it, shifted by whole 128-byte pixel rows,
+// with 8-row groups one box row = 1,280 bytes apart). Every tcgen05.mma is 128 x 256 x 16, the
+// full-rate shape (a 64-channel input gives the M = pixels form 128-wide MMAs that read both
+// operands at the shared-memory bandwidth), and each activation pixel crosses L2 -> shared memory
+// once per tile instead of once per tap. Epilogue as in the pixels-as-N kernel.
+constexpr int kSHTH = 32, kSHTW = 8, kSHBoxW = kSHTW + 2, kSHBoxH = kSHTH + 2;
+constexpr uint32_t kSHBoxBytes = kSHBoxW * kSHBoxH * 128;          // 43,520
+constexpr uint32_t kSHBoxStage = (kSHBoxBytes + 1023u) & ~1023u;   // 44,032
+constexpr int kSHBoxStages = 2;
+constexpr uint32_t kSHWTile = kSwapBN * kBK * 2;                   // 16 KB
+constexpr int kSHWStages = 4;
+constexpr size_t kSHSmem =
+    1024 + kSHBoxStages * kSHBoxStage + kSHWStages * kSHWTile + 8 * kTileT;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_swap_halo_kernel(const __grid_constant__ CUtensorMap tmA,
+                             const __grid_constant__ CUtensorMap tmW, const ConvArgs a,
+                             const TcGeom tg) {
+  constexpr uint32_t TMEM_COLS = 2 * kSwapBP;
+  constexpr uint32_t IDESC = make_idesc(kSwapBP);
+
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bfull[kSHBoxStages], bempty[kSHBoxStages];
+  __shared__ __align__(8) uint64_t wfull[kSHWStages], wempty[kSHWStages];
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
+  const uint32_t box_base = smem_base, w_base = smem_base + kSHBoxStages * kSHBoxStage;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSHBoxStages; s++) {
+      mbar_init(smem_u32(&bfull[s]), 1);
+      mbar_init(smem_u32(&bempty[s]), 1);
+    }
+    for (int s = 0; s < kSHWStages; s++) {
+      mbar_init(smem_u32(&wfull[s]), 1);
+      mbar_init(smem_u32(&wempty[s]), 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(smem_u32(&tfull_bar[i]), 1);
+      mbar_init(smem_u32(&tempty_bar[i]), kEpiThreads / 32);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_base_sh;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: one box per tile, one weight tile per tap ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmW)) : "memory");
+      int bs = 0, ws = 0;
+      uint32_t bph = 0, wph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x) {
+        int b, oy, ox;
+        patch_origin(a, tg, t, b, oy, ox);
+        if (!mbar_wait(smem_u32(&bempty[bs]), bph ^ 1, &abort_flag, a.err)) break;
+        mbar_expect_tx(smem_u32(&bfull[bs]), kSHBoxBytes);
+        tma_load_4d(box_base + bs * kSHBoxStage, &tmA, smem_u32(&bfull[bs]), 0, ox - 1, oy - 1, b);
+        if (++bs == kSHBoxStages) { bs = 0; bph ^= 1; }
+        for (int tap = 0; tap < 9; tap++) {
+          if (!mbar_wait(smem_u32(&wempty[ws]), wph ^ 1, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(smem_u32(&wfull[ws]), kSHWTile);
+          tma_load_2d(w_base + ws * kSHWTile, &tmW, smem_u32(&wfull[ws]), tap * kBK, 0);
+          if (++ws == kSHWStages) { ws = 0; wph ^= 1; }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: D[128 ch][256 px] += W_tap[128 x 64] X_tap[256 x 64]^T ----------
+    if (lane == 0) {
+      int bs = 0, ws = 0, it = 0;
+      uint32_t bph = 0, wph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tg.total && ok; t += gridDim.x, it++) {
+        const int acc = it & 1;
+        const uint32_t use = (uint32_t)(it >> 1);
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
+        tc_fence_after();
+        if (!mbar_wait(smem_u32(&bfull[bs]), bph, &abort_flag, a.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(acc * kSwapBP);
+        // the box's 8-row groups (patch rows) are one box row apart; the swizzle follows
+        // absolute address bits, so shifted starts keep the phase field at 0
+        const uint64_t db0 = sw128_desc_k(box_base + bs * kSHBoxStage, kSHBoxW * 128, 0);
+        for (int tap = 0; tap < 9; tap++) {
+          if (!mbar_wait(smem_u32(&wfull[ws]), wph, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da = sw128_desc(w_base + ws * kSHWTile);
+          const uint64_t db = db0 + (uint64_t)(((tap / 3) * kSHBoxW + tap % 3) * 8);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; k++)
+            mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
+                     (tap > 0 || k > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&wempty[ws]));
+          if (++ws == kSHWStages) { ws = 0; wph ^= 1; }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bempty[bs]));
+        if (++bs == kSHBoxStages) { bs = 0; bph ^= 1; }
+        mma_commit(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..9), as in the pixels-as-N kernel ----------------
+    const int q = warp & 3;            // TMEM lane quarter = channels q*32 .. q*32+31
+    const int half = (warp - 2) >> 2;  // pixels half*128 .. half*128+127 of the patch
+    uint8_t *tsm = smem_gen + kSHBoxStages * kSHBoxStage + kSHWStages * kSHWTile +
+                   (size_t)(warp - 2) * kTileT;
+    int it = 0;
+    for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
+      const int acc = it & 1;
+      const uint32_t use = (uint32_t)(it >> 1);
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1, &abort_flag, a.err);
+      if (!__shfl_sync(0xffffffffu, ready, 0)) break;
+      tc_fence_after();
+      int b, oy, ox;
+      patch_origin(a, tg, t, b, oy, ox);
+      const BlockGeom g = a.geom[b];
+      const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kSwapBP);
+      const int n = q * 32;
+#pragma unroll 1
+      for (int c = half * (kSwapBP / 2); c < (half + 1) * (kSwapBP / 2); c += 32) {
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)c, v);   // v[j] = D[channel n + lane][pixel c + j]
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+          *reinterpret_cast<float *>(tsm + j * 128 + ((((lane >> 2) ^ (j & 7)) << 4) |
+                                                      ((lane & 3) << 2))) = v[j];
+        __syncwarp();
+        const int cg = lane & 3;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int j = k * 8 + (lane >> 2);
+          float r[8];
+          swap_tile_read8(tsm, j, cg, r);
+          const int pp = c + j;
+          const int y = oy + pp / kSHTW, x = ox + pp % kSHTW;
+          if (y < a.Hb && x < a.Wb) epilogue8(a, g, b, y, x, n + cg * 8, r);
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();   // every lane of the warp has finished its TMEM reads
+      if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
 // ---- failure path check ----------------------------------------------------------------------------
 // One CTA waits on an mbarrier that nothing will complete, with the same bounded wait the
 // convolution kernels use but a short limit: the wait runs out, kErrTimeout is latched in the
@@ -1102,13 +1277,56 @@ cudaError_t encode_act_halo(CUtensorMap *m, const void *ptr, int B, int H, int W
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// conv2_1's forward shape (64 -> 128 channels, no fused term): the pixels-as-N halo kernel
+bool swap_halo_shape(const ConvArgs &a) {
+  return a.taps == 9 && a.cin == 64 && a.cout == kSwapBN && a.k2 == 0 && !a.pool_out;
+}
+
+cudaError_t launch_swap_halo(const ConvArgs &a, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_swap_halo_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSHSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (a.tiles && (a.TH != kSHTH || a.TW != kSHTW)) return cudaErrorInvalidValue;
+  CUtensorMap mA, mW;
+  cudaError_t e;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.Wb, (cuuint64_t)a.Hb, (cuuint64_t)a.B};
+    cuuint64_t strides[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.Wb * a.cin * 2,
+                             (cuuint64_t)a.Hb * a.Wb * a.cin * 2};
+    cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kSHBoxW, (cuuint32_t)kSHBoxH, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(a.A), dims,
+                          strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  if ((e = encode_wt(&mW, a.Wt, a.cout, 9 * a.cin, kSwapBN)) != cudaSuccess) return e;
+  TcGeom tg{};
+  tg.TH = kSHTH;
+  tg.TW = kSHTW;
+  tg.tiles_x = (a.Wb + kSHTW - 1) / kSHTW;
+  tg.tiles_y = (a.Hb + kSHTH - 1) / kSHTH;
+  tg.n_tiles = 1;
+  tg.total = a.tiles ? a.n_mtiles : a.B * tg.tiles_x * tg.tiles_y;
+  if (tg.total <= 0) return cudaSuccess;
+  const int grid = std::min(tg.total, g_num_sms);
+  conv_tc_swap_halo_kernel<<<grid, kThreads, kSHSmem, s>>>(mA, mW, a, tg);
+  return cudaGetLastError();
+}
+
 // (cin, cout, k2) of the narrow layers -> N slice width and counts; false if not a halo layer
 bool halo_shape(const ConvArgs &a, int *BN, int *KB, int *P2KB, int *NT) {
   if (a.taps != 9 || a.cin % kBK || a.k2 % kBK) return false;
   *KB = a.cin / kBK;
   *P2KB = a.k2 / kBK;
   if (a.cin == 64 && a.cout == 64 && a.k2 <= 64) { *BN = 64; *NT = 1; return true; }
-  if (a.cin == 64 && a.cout == 128 && a.k2 == 0) { *BN = 128; *NT = 1; return true; }
+  // (conv2_1's forward, 64 -> 128 without a fused term, runs on the pixels-as-N halo kernel)
   if (a.cin == 128 && a.cout == 64 && a.k2 == 0) { *BN = 64; *NT = 1; return true; }
   // (conv2_2, 128 -> 128, runs faster on the pixels-as-N kernel with 256-wide MMAs than here
   // with two 64-wide N slices; conv2_1, 64 -> 128, is faster here: 0.76 against 0.83 ms at
@@ -1159,22 +1377,34 @@ cudaError_t launch_timeout_check(long long limit_cycles, unsigned *err, cudaStre
   return cudaGetLastError();
 }
 
-void conv_tc_patch_rule(int cin, int cout, int taps, int k2, int *rows, bool *fixed) {
+void conv_tc_patch_rule(int cin, int cout, int taps, int k2, bool pool, int *rows, int *fixed_th,
+                        int *fixed_tw) {
   ConvArgs a{};
   a.cin = taps ? cin : 0;
   a.cout = cout;
   a.taps = taps;
   a.k2 = k2;
+  a.pool_out = pool ? reinterpret_cast<void *>(1) : nullptr;   // only tested against null
   int bn, kb, p2, nt;
-  *fixed = halo_shape(a, &bn, &kb, &p2, &nt);
-  *rows = *fixed ? kHaloTH * kHaloTW : (cout == kSwapBN ? kSwapBP : 128);
+  *fixed_th = *fixed_tw = 0;
+  if (swap_halo_shape(a)) {
+    *rows = kSwapBP;
+    *fixed_th = kSHTH;
+    *fixed_tw = kSHTW;
+  } else if (halo_shape(a, &bn, &kb, &p2, &nt)) {
+    *rows = kHaloTH * kHaloTW;
+    *fixed_th = kHaloTH;
+    *fixed_tw = kHaloTW;
+  } else {
+    *rows = cout == kSwapBN ? kSwapBP : 128;
+  }
 }
 
-void conv_tc_pick_patch(const int *h, const int *w, int n, int rows, bool fixed, bool pool,
-                        int *TH, int *TW) {
-  if (fixed) {
-    *TH = kHaloTH;
-    *TW = kHaloTW;
+void conv_tc_pick_patch(const int *h, const int *w, int n, int rows, int fixed_th, int fixed_tw,
+                        bool pool, int *TH, int *TW) {
+  if (fixed_th) {
+    *TH = fixed_th;
+    *TW = fixed_tw;
     return;
   }
   pick_patch_multi(h, w, n, rows, pool, *TH, *TW);
@@ -1185,6 +1415,7 @@ cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s) {
   if ((a.taps != 0 && a.taps != 9) || a.cout % 64 || (a.taps && a.cin % 64) || a.k2 % 64 ||
       (a.taps == 0 && a.k2 == 0))
     return cudaErrorInvalidValue;
+  if (swap_halo_shape(a)) return launch_swap_halo(a, s);
   int hBN, hKB, hP2, hNT;
   if (halo_shape(a, &hBN, &hKB, &hP2, &hNT)) {
     if (a.tiles && (a.TH != kHaloTH || a.TW != kHaloTW)) return cudaErrorInvalidValue;

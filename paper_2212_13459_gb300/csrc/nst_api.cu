@@ -509,9 +509,8 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
   auto add_list = [&](const Batch &bt, int level, int cin, int cout, int taps, int k2, bool pool,
                       auto pick) -> PatchList {
     PatchList pl{(int)patches.size(), 0, 0, 0};
-    int rows;
-    bool fixed;
-    conv_tc_patch_rule(cin, cout, taps, k2, &rows, &fixed);
+    int rows, fth, ftw;
+    conv_tc_patch_rule(cin, cout, taps, k2, pool, &rows, &fth, &ftw);
     std::vector<Iv> ry(bt.B), rx(bt.B);
     std::vector<int> hs(bt.B), wsz(bt.B);
     for (int j = 0; j < bt.B; j++) {
@@ -523,7 +522,7 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
       hs[j] = std::max(0, ry[j].b - ry[j].a);
       wsz[j] = std::max(0, rx[j].b - rx[j].a);
     }
-    conv_tc_pick_patch(hs.data(), wsz.data(), bt.B, rows, fixed, pool, &pl.TH, &pl.TW);
+    conv_tc_pick_patch(hs.data(), wsz.data(), bt.B, rows, fth, ftw, pool, &pl.TH, &pl.TW);
     for (int j = 0; j < bt.B; j++)
       for (int y = ry[j].a; y < ry[j].b; y += pl.TH)
         for (int x = rx[j].a; x < rx[j].b; x += pl.TW) patches.push_back(make_int4(j, y, x, 0));

@@ -90,14 +90,16 @@ void launch_finish_loss(const double *parts, double *loss, cudaStream_t s);
 // k_tc.cu: tcgen05 / TMEM / TMA implicit-GEMM convolution (BF16 in, FP32 accumulate)
 // Returns cudaSuccess or the error of tensor-map encoding / launch.
 cudaError_t launch_conv_tc(const ConvArgs &a, cudaStream_t s);
-// Patch rule of the tensor-core convolution that a launch of this shape runs: fixed 16 x 8
-// patches (*fixed, the halo kernel of the 64-channel layers) or any TH x TW with
-// TH * TW <= *rows pixels (128; 256 for the pixels-as-N kernel of 128-channel outputs).
-void conv_tc_patch_rule(int cin, int cout, int taps, int k2, int *rows, bool *fixed);
+// Patch rule of the tensor-core convolution that a launch of this shape runs: a fixed
+// *fixed_th x *fixed_tw patch (16 x 8 for the 64-channel halo kernel, 32 x 8 for the
+// pixels-as-N halo kernel of conv2_1's forward; 0 = free) or any TH x TW with TH * TW <= *rows
+// pixels (128; 256 for the pixels-as-N kernel of 128-channel outputs). pool: fused pooling.
+void conv_tc_patch_rule(int cin, int cout, int taps, int k2, bool pool, int *rows, int *fixed_th,
+                        int *fixed_tw);
 // The patch shape within that rule that covers n rectangles h[i] x w[i] with the fewest
 // patches (with fused pooling TW is 8 or 16 and TH * TW = rows).
-void conv_tc_pick_patch(const int *h, const int *w, int n, int rows, bool fixed, bool pool,
-                        int *TH, int *TW);
+void conv_tc_pick_patch(const int *h, const int *w, int n, int rows, int fixed_th, int fixed_tw,
+                        bool pool, int *TH, int *TW);
 bool tc_available();
 void *tc_encode_tiled_fn();   // cuTensorMapEncodeTiled (driver entry point), null if unavailable
 int tc_num_sms();

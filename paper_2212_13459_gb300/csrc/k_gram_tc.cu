@@ -8,6 +8,9 @@
 // own tensor map whose bounds are its owned rectangle, so pixels outside it read as zero and
 // never enter the sum. Every CTA accumulates one (I, J) tile over one run of boxes in TMEM
 // (FP32) and writes it out; a fixed-order FP64 reduction adds the runs (deterministic).
+// When the I tile's channels are among the J tile's (C <= 128, and the diagonal tiles of
+// larger C), the A operand is read from the B slabs already in shared memory instead of being
+// loaded again; A channels past C (C = 64) read a slab of zeros written once per CTA.
 #include <algorithm>
 
 #include "nst_internal.cuh"
@@ -28,6 +31,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
   constexpr uint32_t A_BYTES = 2 * kSlab;
   constexpr uint32_t B_BYTES = (N / 64) * kSlab;
   constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t ZERO_OFF = kStages * STAGE_BYTES;   // one slab of zeros after the stages
   constexpr uint32_t TMEM_COLS = N;
   // kind::f16, FP32 D, BF16 A/B, both MN-major, M = 128, N
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
@@ -43,6 +47,18 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
   const GramTcChunk ch = a.chunks[blockIdx.x];
   const int tile = blockIdx.y, I = tile / a.nJ, J = tile % a.nJ;
   const CUtensorMap *map = a.maps + ch.b;
+  // A slab s (channels I*128 + 64 s ..) is B slab (I*128 + 64 s - J*N) / 64 when it lies inside
+  // the J tile, zeros when it lies past C, else loaded
+  int a_src[2];
+  bool a_load = false;
+#pragma unroll
+  for (int sl = 0; sl < 2; sl++) {
+    const int c0 = I * 128 + 64 * sl;
+    if (c0 >= a.C) a_src[sl] = -2;                                   // zeros
+    else if (c0 >= J * N && c0 + 64 <= J * N + N) a_src[sl] = (c0 - J * N) / 64;   // B slab
+    else { a_src[sl] = -1; a_load = true; }                          // own A slab
+  }
+  const uint32_t tx_bytes = B_BYTES + (a_load ? A_BYTES : 0u);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) {
@@ -52,6 +68,12 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
     mbar_init(smem_u32(&done_bar), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (a_src[0] == -2 || a_src[1] == -2) {   // the zero slab (read by the MMAs only)
+    uint8_t *z = smem_raw + (smem_base - smem_u32(smem_raw)) + ZERO_OFF;
+    for (int i = threadIdx.x; i < (int)(kSlab / 16); i += kThreads)
+      *reinterpret_cast<uint4 *>(z + (size_t)i * 16) = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_smem();
   }
   if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), TMEM_COLS);
   tc_fence_before();
@@ -68,9 +90,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
         const uint32_t fb = smem_u32(&full_bar[stage]);
         const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
         const int x = (k % ch.nbx) * a.TW, y = (k / ch.nbx) * a.TH;
-        mbar_expect_tx(fb, STAGE_BYTES);
-        tma_load_4d(sa, map, fb, I * 128, x, y, 0);
-        tma_load_4d(sa + kSlab, map, fb, I * 128 + 64, x, y, 0);
+        mbar_expect_tx(fb, tx_bytes);
+        if (a_load) {
+          tma_load_4d(sa, map, fb, I * 128, x, y, 0);
+          tma_load_4d(sa + kSlab, map, fb, I * 128 + 64, x, y, 0);
+        }
 #pragma unroll
         for (int j = 0; j < N / 64; j++) tma_load_4d(sb + j * kSlab, map, fb, J * N + j * 64, x, y, 0);
         if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -88,9 +112,18 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
         }
         tc_fence_after();
         const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
+        // A's two 64-channel atoms: its own slabs, B slabs, or the zero slab (after every stage,
+        // so the atom distance, the descriptor's leading byte offset, stays positive)
+        uint32_t a0 = sa, lbo = kSlab;
+        if (!a_load) {
+          a0 = a_src[0] >= 0 ? sb + (uint32_t)a_src[0] * kSlab : smem_base + ZERO_OFF;
+          const uint32_t a1 =
+              a_src[1] >= 0 ? sb + (uint32_t)a_src[1] * kSlab : smem_base + ZERO_OFF;
+          lbo = a1 - a0;
+        }
 #pragma unroll
         for (int kk = 0; kk < 4; kk++)   // 16 pixels (two 8-row groups) per MMA
-          mma_bf16(tmem_base, sw128_desc_mn(sa + kk * 2048, kSlab),
+          mma_bf16(tmem_base, sw128_desc_mn(a0 + kk * 2048, lbo),
                    sw128_desc_mn(sb + kk * 2048, kSlab), IDESC,
                    (k > ch.box0 || kk > 0) ? 1u : 0u);
         mma_commit(smem_u32(&empty_bar[stage]));
@@ -173,7 +206,7 @@ __global__ void __launch_bounds__(256) gram_tc_reduce_kernel(const float *__rest
 
 template <int N>
 cudaError_t launch_n(const GramTcArgs &a, int nruns, cudaStream_t s) {
-  constexpr size_t smem = (size_t)kStages * (2 * kSlab + (N / 64) * kSlab) + 1024;
+  constexpr size_t smem = (size_t)kStages * (2 * kSlab + (N / 64) * kSlab) + kSlab + 1024;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<N>,

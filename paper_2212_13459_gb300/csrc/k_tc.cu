@@ -165,13 +165,9 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
 }
 
 // ---- fused 2x2 max pooling in the forward epilogue ---------------------------------------------
-// The four pixels of a pooling window are rows (y, x), (y, x+1), (y+1, x), (y+1, x+1) of the
-// output patch. With 8- or 16-pixel-wide patches and 32 rows per epilogue warp they sit in one
-// warp at lanes l, l^1, l^TW, l^(TW+1): the max is two shuffles, and the window's top-left lane
-// writes the pooled value. Outside the block's valid pooled region the pooled map is zero.
-//
-// The decision is taken on the FP32 activations (accumulator + bias, ReLU), before they are
-// rounded for storage: rounding to BF16 merges values that differ by less than half an ulp
+// Outside the block's valid pooled region the pooled map is zero. The decision is taken on the
+// FP32 activations (accumulator + bias, ReLU), before they are rounded for storage: rounding to
+// BF16 merges values that differ by less than half an ulp
 // (2^-9 relative), which at a smooth input would turn most windows into exact ties. The pooled
 // value is the window max rounded once to BF16; as rounding is monotone, that equals pooling
 // the rounded activations.
@@ -184,50 +180,72 @@ __device__ __forceinline__ void epilogue32(const ConvArgs &a, const BlockGeom &g
 // 8 (k & 3) + 4 (k >> 2).
 __device__ __forceinline__ uint32_t pool_nibble_shift(int k) { return 8 * (k & 3) + 4 * (k >> 2); }
 
-__device__ __forceinline__ void pool_epilogue32(const ConvArgs &a, const BlockGeom &g, int b,
-                                                int y, int x, int n, int tw, const float *v) {
-  constexpr int NC = 32, NW = NC / 2;   // channels, BF16 pairs
-  // FP32 max over the window with 2 shuffles per channel, which leave it in all four lanes
-  float m[NC];
+// ---- fused 2x2 max pooling of the 64-channel halo kernel, read in the 16x256b layout ------------
+// Forward of a 64-channel layer followed by pooling (conv1_2) on 16 x 8 patches: TMEM lane L =
+// patch pixel (L / 8, L % 8). One 16x256b read of the 16 lanes 16g .. 16g + 15 of this warp's
+// quarter gives thread t the pixels (2r, c) and (2r + 1, c), r = the lanes' pixel-row pair,
+// c = t / 4, i.e. the two vertically adjacent pixels of a pooling-window column, for the channel
+// pairs 8k + 2(t % 4), +1 (k = 0..3) of the 32 channels at n. The vertical half of each window
+// max is in registers, the horizontal half one shuffle away (thread t ^ 4 holds column c ^ 1),
+// and the pooled BF16 pairs are formed in place. Bias + ReLU in FP32, zero outside the valid
+// region, first maximum decided on the FP32 values, the max rounded once (as in swap_pool8).
+__device__ __forceinline__ void halo_pool16(const ConvArgs &a, const BlockGeom &g, int b, int py0,
+                                            int px0, int n, uint32_t taddr) {
+  const int t = threadIdx.x & 31, j = t & 3, c = t >> 2;   // j: channel pair, c: patch column
+  float v[16];
+  tmem_ld16x256b_x4(taddr, v);
+  const int y0 = py0, x = px0 + c;   // top pixel of this thread's column pair (y0 even)
+  const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
+  const bool vt = y0 < ehl && x < ewl, vb = y0 + 1 < ehl && x < ewl;
+  float m[8];
 #pragma unroll
-  for (int j = 0; j < NC; j++) {
-    const float m1 = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
-    m[j] = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, tw));
-  }
-  uint32_t idx[NC / 8];
-  if (a.pool_idx) {
-    const int qpos = (x & 1) | ((y & 1) << 1);
+  for (int k = 0; k < 4; k++) {
+    const float2 bb = __ldg(reinterpret_cast<const float2 *>(a.bias + n + 8 * k + 2 * j));
 #pragma unroll
-    for (int i = 0; i < NC / 8; i++) {
-      uint32_t w = 0u;
-#pragma unroll
-      for (int k = 0; k < 8; k++)
-        w |= (v[8 * i + k] == m[8 * i + k] && m[8 * i + k] > 0.f) ? 1u << pool_nibble_shift(k)
-                                                                   : 0u;
-      w <<= qpos;
-      w |= __shfl_xor_sync(0xffffffffu, w, 1);
-      w |= __shfl_xor_sync(0xffffffffu, w, tw);
-      idx[i] = w;
+    for (int e = 0; e < 2; e++) {
+      const float bias = e ? bb.y : bb.x;
+      float &top = v[4 * k + e], &bot = v[4 * k + 2 + e];
+      top = vt ? fmaxf(top + bias, 0.f) : 0.f;
+      bot = vb ? fmaxf(bot + bias, 0.f) : 0.f;
+      const float mv = fmaxf(top, bot);
+      m[2 * k + e] = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, 4));
     }
   }
-  uint32_t h[NW];
+  const bool left = !(c & 1);
+  uint32_t idx[4];
+  if (a.pool_idx) {
+    const int qt = left ? 0 : 1;   // window positions of this thread's top / bottom pixel
 #pragma unroll
-  for (int j = 0; j < NW; j++) {
-    const __nv_bfloat162 p = __floats2bfloat162_rn(m[2 * j], m[2 * j + 1]);
-    h[j] = *reinterpret_cast<const uint32_t *>(&p);
+    for (int k = 0; k < 4; k++) {
+      uint32_t w = 0u;
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const float mm = m[2 * k + e];
+        const uint32_t sh = pool_nibble_shift(2 * j + e) + qt;
+        w |= (v[4 * k + e] == mm && mm > 0.f) ? 1u << sh : 0u;
+        w |= (v[4 * k + 2 + e] == mm && mm > 0.f) ? 1u << (sh + 2) : 0u;
+      }
+      w |= __shfl_xor_sync(0xffffffffu, w, 4);   // the window's other column
+      w |= __shfl_xor_sync(0xffffffffu, w, 1);   // the other channel pairs of the group
+      w |= __shfl_xor_sync(0xffffffffu, w, 2);
+      idx[k] = w;
+    }
   }
-  if ((y & 1) || (x & 1) || y >= a.Hb || x >= a.Wb) return;
-  const int py = y >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
+  if (!left) return;
+  const int py = y0 >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
+  if (py >= Hp || px >= Wp) return;
   const bool valid = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
   const size_t po = (((size_t)b * Hp + py) * Wp + px) * a.cout + n;
-  if (a.pool_idx)
+  if (a.pool_idx && j == 0)
     *reinterpret_cast<uint4 *>(a.pool_idx + po / 2) =
         valid ? make_uint4(idx[0], idx[1], idx[2], idx[3]) : make_uint4(0u, 0u, 0u, 0u);
-  uint4 *out = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + po);
+  __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + po + 2 * j;
 #pragma unroll
-  for (int q = 0; q < NC / 8; q++)
-    out[q] = valid ? make_uint4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3])
-                   : make_uint4(0u, 0u, 0u, 0u);
+  for (int k = 0; k < 4; k++) {
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(valid ? m[2 * k] : 0.f,
+                                                   valid ? m[2 * k + 1] : 0.f);
+    *reinterpret_cast<__nv_bfloat162 *>(out + 8 * k) = p2;
+  }
 }
 
 // ---- epilogue through a per-warp transpose tile -----------------------------------------------------
@@ -333,7 +351,7 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
   }
   const size_t po = (((size_t)b * Hp + py) * Wp + px) * a.cout + n + cg * 8;
   st_bf16x8(reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + po, m);
-  if (a.pool_idx) {   // window positions, in the format of pool_epilogue32 (first max only)
+  if (a.pool_idx) {   // window positions, in the nibble format above (first max only)
     uint32_t w = 0u;
 #pragma unroll
     for (int i = 0; i < 8; i++)
@@ -715,17 +733,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                (size_t)pbox * 128;
         mswz = pbox & 7;
       }
+      if (a.pool_out) {
+        // pooled forward: two 16-lane reads of the 16x256b layout (pixel-row pairs 4q, 4q + 2)
 #pragma unroll 1
-      for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
-        float v[32];
-        tmem_ld32(tbase + (uint32_t)c, v);
-        if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v, mrow, mswz);
-        if (a.pool_out) {
-          if (!inb) {
+        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32)
 #pragma unroll
-            for (int j = 0; j < 32; j++) v[j] = 0.f;
-          }
-          pool_epilogue32(a, g, b, y, x, nt * BN + c, kHaloTW, v);
+          for (int grp = 0; grp < 2; grp++)
+            halo_pool16(a, g, b, oy + 4 * q + 2 * grp, ox, nt * BN + c,
+                        tbase + ((uint32_t)(16 * grp) << 16) + (uint32_t)c);
+      } else {
+#pragma unroll 1
+        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+          float v[32];
+          tmem_ld32(tbase + (uint32_t)c, v);
+          if (inb) epilogue32(a, g, b, y, x, nt * BN + c, v, mrow, mswz);
         }
       }
       tc_fence_before();

@@ -190,6 +190,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 TMEM lanes x 32 FP32 columns in the 16x256b layout: thread t holds lanes t/4 and t/4 + 8
+// (of the 16 at taddr) and, for each 8-column unit k, columns 8k + 2(t%4) and 8k + 2(t%4) + 1:
+// v[4k] = (t/4, c), v[4k+1] = (t/4, c+1), v[4k+2] = (t/4+8, c), v[4k+3] = (t/4+8, c+1)
+__device__ __forceinline__ void tmem_ld16x256b_x4(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
 // tcgen05.mma kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
 // M = 128, N = n (a multiple of 16, 16..256)
 __host__ __device__ constexpr uint32_t idesc_bf16_m128(int n) {

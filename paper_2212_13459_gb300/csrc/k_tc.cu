@@ -543,7 +543,10 @@ struct HaloCfg {
   static constexpr uint32_t TILE_B = BN * 128;                  // one (tap, K-block) weight tile
   static constexpr uint32_t W_BYTES = (9 * KB + P2KB) * TILE_B;
   static constexpr int STAGES_RAW = (int)((kHaloSmemMax - 1024 - W_BYTES) / kHaloStage);
-  static constexpr int STAGES = STAGES_RAW > 4 ? 4 : STAGES_RAW;
+  // two boxes per tile (the fused V R phase) get three tiles in flight; one box per tile keeps
+  // four stages (six measured slower on conv1_2's forward, faster on its input gradient)
+  static constexpr int CAP = P2KB ? 6 : 4;
+  static constexpr int STAGES = STAGES_RAW > CAP ? CAP : STAGES_RAW;
   static constexpr size_t SMEM = 1024 + W_BYTES + (size_t)STAGES * kHaloStage;
 };
 

@@ -31,7 +31,6 @@ def seeded(H, W, seed, Hv=None, Wv=None, noise=0.1, bias_std=0.0):
 # its path), 0.11 / 0.18 / 0.22 / 0.32 for the ReLU2_1 .. ReLU5_1 terms. The GPU's BF16 form is
 # therefore held, case by case, to FLOOR_FACTOR times the deviation that BF16 storage causes in
 # the oracle itself on the same input (never below TOL_BF16): see bf16_grad_bound().
-TOL_BF16_FULL_GRAD = 0.35   # a fixed bound, only where no oracle floor is at hand
 FLOOR_FACTOR = 1.5
 STYLE1_ONLY = (0.2, 0.0, 0.0, 0.0, 0.0)
 

@@ -7,7 +7,7 @@
 // swizzle). One TMA box of 64 pixels feeds every operand slab of a K step. Each block gets its
 // own tensor map whose bounds are its owned rectangle, so pixels outside it read as zero and
 // never enter the sum. Every CTA accumulates one (I, J) tile over one run of boxes in TMEM
-// (FP32) and writes it out; a fixed-order FP64 reduction adds the runs (deterministic).
+// (FP32) and writes it out; a fixed-order compensated reduction adds the runs (deterministic).
 // When the I tile's channels are among the J tile's (C <= 128, and the diagonal tiles of
 // larger C), the A operand is read from the B slabs already in shared memory instead of being
 // loaded again; A channels past C (C = 64) read a slab of zeros written once per CTA.
@@ -161,44 +161,79 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
   }
 }
 
-// Gacc[i][j] += sum over runs (fixed order, FP64) of the FP32 tile partials. A CTA takes 32
-// consecutive elements (one per lane, coalesced reads); its 8 warps split the runs (warp w sums
-// runs w, w + 8, ... in order) and the 8 partial sums are added in warp order (deterministic).
-// A warp issues the loads of up to 8 of its runs before adding them (in run order), so the
-// loads are in flight together instead of one after another.
-__global__ void __launch_bounds__(256) gram_tc_reduce_kernel(const float *__restrict__ part,
-                                                             int nruns, int C, int N, int nI,
-                                                             int nJ, double *__restrict__ Gacc) {
-  __shared__ double red[8][32];
+// Compensated FP32 addition (Knuth's TwoSum): s + c carries the sum of every added value with
+// the rounding error of each addition kept in c, so the pair is as exact as an FP64 sum of the
+// FP32 inputs up to O(n u^2) (u = 2^-24) and costs seven FP32 operations, where the FP64 unit of
+// this GPU retires a few operations per SM and clock.
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
+  const float t = s + x;
+  const float z = t - s;
+  c += (s - (t - z)) + (x - z);
+  s = t;
+}
+
+// Gacc[i][j] += sum over runs (fixed order, compensated FP32, then FP64) of the FP32 tile
+// partials. A CTA takes 32 V consecutive elements (V per lane: one float4 load per run when
+// V = 4, coalesced); its NW warps split the runs (warp w sums runs w, w + NW, ... in order) and
+// the NW partial pairs are added in warp order (deterministic); each element's pair is converted
+// to FP64 once and added to Gacc. A warp issues the loads of up to 8 of its runs before adding
+// them (in run order), so the loads are in flight together instead of one after another.
+// C^2 is a multiple of 4096 and V consecutive elements stay inside one N-wide tile row, so the
+// V elements of a lane are contiguous in every run's partial.
+template <int V, int NW>
+__global__ void __launch_bounds__(NW * 32) gram_tc_reduce_kernel(const float *__restrict__ part,
+                                                                 int nruns, int C, int N, int nI,
+                                                                 int nJ,
+                                                                 double *__restrict__ Gacc) {
+  __shared__ float2 red[NW][32 * V];
   const long long n = (long long)C * C;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t stride = (size_t)nI * nJ * 128 * N;
-  for (long long e0 = (long long)blockIdx.x * 32; e0 < n; e0 += (long long)gridDim.x * 32) {
-    const long long e = e0 + lane;
-    double s = 0.0;
+  for (long long e0 = (long long)blockIdx.x * 32 * V; e0 < n;
+       e0 += (long long)gridDim.x * 32 * V) {
+    const long long e = e0 + (long long)lane * V;
+    float s[V], c[V];
+#pragma unroll
+    for (int k = 0; k < V; k++) s[k] = c[k] = 0.f;
     if (e < n) {
       const int i = (int)(e / C), j = (int)(e % C);
       const int tile = (i / 128) * nJ + j / N;
       const size_t off = ((size_t)tile * 128 + (i % 128)) * N + (j % N);
-      for (int r0 = warp; r0 < nruns; r0 += 64) {
-        float v[8];
+      for (int r0 = warp; r0 < nruns; r0 += 8 * NW) {
+        float v[8][V];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
-          const int r = r0 + 8 * u;
-          v[u] = r < nruns ? __ldg(part + (size_t)r * stride + off) : 0.f;
+          const int r = r0 + NW * u;
+          if constexpr (V == 4) {
+            const float4 q = r < nruns
+                                 ? __ldg(reinterpret_cast<const float4 *>(part + (size_t)r * stride + off))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u][0] = q.x; v[u][1] = q.y; v[u][2] = q.z; v[u][3] = q.w;
+          } else {
+            v[u][0] = r < nruns ? __ldg(part + (size_t)r * stride + off) : 0.f;
+          }
         }
 #pragma unroll
         for (int u = 0; u < 8; u++)
-          if (r0 + 8 * u < nruns) s += (double)v[u];
+          if (r0 + NW * u < nruns)
+#pragma unroll
+            for (int k = 0; k < V; k++) two_sum_add(s[k], c[k], v[u][k]);
       }
     }
-    red[warp][lane] = s;
-    __syncthreads();
-    if (warp == 0 && e < n) {
-      double t = 0.0;
 #pragma unroll
-      for (int w = 0; w < 8; w++) t += red[w][lane];
-      Gacc[e] += t;
+    for (int k = 0; k < V; k++) red[warp][lane * V + k] = make_float2(s[k], c[k]);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 32 * V; q += NW * 32) {
+      if (e0 + q < n) {
+        float ts = 0.f, tc = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+          const float2 p = red[w][q];
+          two_sum_add(ts, tc, p.x);
+          tc += p.y;
+        }
+        Gacc[e0 + q] += (double)ts + (double)tc;
+      }
     }
     __syncthreads();
   }
@@ -267,9 +302,17 @@ cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStr
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  // float4 lanes where that still gives two CTAs per SM; otherwise one element per lane and 16
+  // warps per CTA splitting the runs (C = 64, 128: few elements, several hundred runs)
   const long long n = (long long)a.C * a.C;
-  const int grid = (int)std::min<long long>((n + 31) / 32, 152 * 8);
-  gram_tc_reduce_kernel<<<grid, 256, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
+  const int sms = tc_num_sms();
+  if (n / 128 >= 2LL * sms) {
+    const int grid = (int)std::min<long long>(n / 128, 8LL * sms);
+    gram_tc_reduce_kernel<4, 8><<<grid, 256, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
+  } else {
+    const int grid = (int)std::min<long long>(n / 32, 4LL * sms);
+    gram_tc_reduce_kernel<1, 16><<<grid, 512, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
+  }
   return cudaGetLastError();
 }
 

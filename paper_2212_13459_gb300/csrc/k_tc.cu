@@ -189,6 +189,13 @@ __device__ __forceinline__ uint32_t pool_nibble_shift(int k) { return 8 * (k & 3
 // max is in registers, the horizontal half one shuffle away (thread t ^ 4 holds column c ^ 1),
 // and the pooled BF16 pairs are formed in place. Bias + ReLU in FP32, zero outside the valid
 // region, first maximum decided on the FP32 values, the max rounded once (as in swap_pool8).
+//
+// Window positions: the 8 threads of a window pair (t / 8 equal) hold disjoint bits of the four
+// 32-bit words of its 32 channels (thread t: channels 8k + 2(t % 4), +1 of word k, its column's
+// two pixels). A reduce-scatter leaves word j = t % 4 at thread t, OR-ed over the channel pairs
+// (exchanges with t ^ 2, then t ^ 1, each passing on the words the partner keeps) and over the
+// window's two columns (t ^ 4): 4 shuffles where an OR of all four words at every thread takes 12.
+// (Reading both 16-lane halves behind one wait and interleaving them measured 6-7 % slower.)
 __device__ __forceinline__ void halo_pool16(const ConvArgs &a, const BlockGeom &g, int b, int py0,
                                             int px0, int n, uint32_t taddr) {
   const int t = threadIdx.x & 31, j = t & 3, c = t >> 2;   // j: channel pair, c: patch column
@@ -212,33 +219,38 @@ __device__ __forceinline__ void halo_pool16(const ConvArgs &a, const BlockGeom &
     }
   }
   const bool left = !(c & 1);
-  uint32_t idx[4];
+  uint32_t idx = 0u;
   if (a.pool_idx) {
     const int qt = left ? 0 : 1;   // window positions of this thread's top / bottom pixel
+    uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      uint32_t w = 0u;
+      w[k] = 0u;
 #pragma unroll
       for (int e = 0; e < 2; e++) {
         const float mm = m[2 * k + e];
         const uint32_t sh = pool_nibble_shift(2 * j + e) + qt;
-        w |= (v[4 * k + e] == mm && mm > 0.f) ? 1u << sh : 0u;
-        w |= (v[4 * k + 2 + e] == mm && mm > 0.f) ? 1u << (sh + 2) : 0u;
+        w[k] |= (v[4 * k + e] == mm && mm > 0.f) ? 1u << sh : 0u;
+        w[k] |= (v[4 * k + 2 + e] == mm && mm > 0.f) ? 1u << (sh + 2) : 0u;
       }
-      w |= __shfl_xor_sync(0xffffffffu, w, 4);   // the window's other column
-      w |= __shfl_xor_sync(0xffffffffu, w, 1);   // the other channel pairs of the group
-      w |= __shfl_xor_sync(0xffffffffu, w, 2);
-      idx[k] = w;
     }
+    // keep words {0, 1} (j < 2) or {2, 3}; pass the other two to t ^ 2
+    const bool hi = (j & 2) != 0, odd = (j & 1) != 0;
+    uint32_t k0 = hi ? w[2] : w[0], k1 = hi ? w[3] : w[1];
+    k0 |= __shfl_xor_sync(0xffffffffu, hi ? w[0] : w[2], 2);
+    k1 |= __shfl_xor_sync(0xffffffffu, hi ? w[1] : w[3], 2);
+    // keep word j; pass the other to t ^ 1
+    uint32_t kj = odd ? k1 : k0;
+    kj |= __shfl_xor_sync(0xffffffffu, odd ? k0 : k1, 1);
+    idx = kj | __shfl_xor_sync(0xffffffffu, kj, 4);   // the window's other column
   }
   if (!left) return;
   const int py = y0 >> 1, px = x >> 1, Hp = a.Hb >> 1, Wp = a.Wb >> 1;
   if (py >= Hp || px >= Wp) return;
   const bool valid = py < (g.eh >> (a.level + 1)) && px < (g.ew >> (a.level + 1));
   const size_t po = (((size_t)b * Hp + py) * Wp + px) * a.cout + n;
-  if (a.pool_idx && j == 0)
-    *reinterpret_cast<uint4 *>(a.pool_idx + po / 2) =
-        valid ? make_uint4(idx[0], idx[1], idx[2], idx[3]) : make_uint4(0u, 0u, 0u, 0u);
+  if (a.pool_idx)   // word j: channels n + 8j .. n + 8j + 7
+    *reinterpret_cast<uint32_t *>(a.pool_idx + po / 2 + 4 * j) = valid ? idx : 0u;
   __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(a.pool_out) + po + 2 * j;
 #pragma unroll
   for (int k = 0; k < 4; k++) {
@@ -639,10 +651,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    // The whole warp runs the issue loop, so its descriptor arithmetic is warp-uniform, and one
-    // elected lane issues each MMA and commit: a loop run by a single lane issues several times
-    // slower once epilogue warps keep this warp's scheduler busy, and a 64-wide MMA takes only
-    // 48 cycles. (The 256-wide MMAs of the other kernels take 128 cycles; there the single-lane
+    // The whole warp runs the issue loop (its waits and loop control are warp-uniform), and one
+    // elected lane issues each K-block's MMAs and commit: a loop run by a single lane issues
+    // several times slower once epilogue warps keep this warp's scheduler busy, and a 64-wide
+    // MMA takes only 48 cycles. (The 256-wide MMAs of the other kernels take 128 cycles; there the single-lane
     // loop keeps up and measured slightly faster.)
     bool ok = mbar_wait_warp(smem_u32(&w_bar), 0, &abort_flag, a.err);
     int stage = 0;
@@ -654,7 +666,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait_warp(smem_u32(&tempty_bar[acc]), (use & 1) ^ 1, &abort_flag, a.err)) break;
       tc_fence_after();
       const uint32_t d = tmem_base + (uint32_t)(acc * BN);
-      bool first = true;
       for (int kb = 0; kb < KBT; kb++) {
         if (!mbar_wait_warp(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
           ok = false;
@@ -665,34 +676,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         // shifted by whole 128-byte rows; the swizzle follows absolute address bits, so the
         // phase field stays 0 (the box itself starts 1024-aligned). Descriptors are the stage's
         // base descriptors plus compile-time offsets (address field in 16-byte units).
-        const uint64_t da0 = sw128_desc_k(sa, kHaloBoxW * 128, 0);
-        if (kb < KB) {
-          const uint64_t db0 = sw128_desc(w_base + kb * Cfg::TILE_B);
+        // One lane (the same one each time) is elected per K-block and issues its unrolled run
+        // of MMAs and the commit: one branch per K-block instead of one per MMA.
+        if (elect_one()) {
+          const uint64_t da0 = sw128_desc_k(sa, kHaloBoxW * 128, 0);
+          if (kb < KB) {
+            const uint64_t db0 = sw128_desc(w_base + kb * Cfg::TILE_B);
 #pragma unroll
-          for (int tap = 0; tap < 9; tap++) {
-            const uint64_t da = da0 + (uint64_t)(((tap / 3) * kHaloBoxW + tap % 3) * 8);
-            const uint64_t db = db0 + (uint64_t)(tap * KB * (Cfg::TILE_B >> 4));
+            for (int tap = 0; tap < 9; tap++) {
+              const uint64_t da = da0 + (uint64_t)(((tap / 3) * kHaloBoxW + tap % 3) * 8);
+              const uint64_t db = db0 + (uint64_t)(tap * KB * (Cfg::TILE_B >> 4));
 #pragma unroll
-            for (int k = 0; k < kBK / 16; k++) {
-              if (elect_one())
+              for (int k = 0; k < kBK / 16; k++)
                 mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC,
-                         first ? 0u : 1u);
-              first = false;
+                         kb == 0 && tap == 0 && k == 0 ? 0u : 1u);
             }
-          }
-        } else {   // phase 2: the V R term, centre tap only
-          const uint64_t da = da0 + (uint64_t)((kHaloBoxW + 1) * 8);
-          const uint64_t db = sw128_desc(w_base + (9 * KB + kb - KB) * Cfg::TILE_B);
+          } else {   // phase 2: the V R term, centre tap only (after phase 1: accumulate)
+            const uint64_t da = da0 + (uint64_t)((kHaloBoxW + 1) * 8);
+            const uint64_t db = sw128_desc(w_base + (9 * KB + kb - KB) * Cfg::TILE_B);
 #pragma unroll
-          for (int k = 0; k < kBK / 16; k++) {
-            if (elect_one())
-              mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, first ? 0u : 1u);
-            first = false;
+            for (int k = 0; k < kBK / 16; k++)
+              mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, 1u);
           }
+          if (!(MASK_SMEM && kb == KB))   // (that box is released by the epilogue)
+            mma_commit(smem_u32(&empty_bar[stage]));
         }
-        if (!(MASK_SMEM && kb == KB)) {   // (that box is released by the epilogue)
-          if (elect_one()) mma_commit(smem_u32(&empty_bar[stage]));
-        }
+        __syncwarp();
         if (++stage == STAGES) { stage = 0; phase ^= 1; }
       }
       if (!ok) break;

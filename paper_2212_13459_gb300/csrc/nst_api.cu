@@ -2,7 +2,7 @@
 //
 // One evaluation of Algorithm 1 (Section 4.2) is
 //   Step 1: for every batch of blocks (extended by margin1): VGG-19 forward to ReLU5_1, Gram partial
-//           sums of the owned pixels at the five style layers, FP64 reduction into G^L(x);
+//           sums of the owned pixels at the five style layers, reduced into G^L(x) (FP64);
 //           then E_style and the style residuals R_L = (4 w_L / n_p)(G^L(x) - G^L(v)) (Eq. 3,
 //           Table 1 row 2);
 //   Step 2: for every batch of blocks (extended by margin2): forward again keeping activations,

@@ -1,11 +1,11 @@
 """Bitwise reproducibility of nst_loss_grad.
 
-Every reduction of the path runs in a fixed order (Gram partial tiles reduced in FP64 by chunk
-index, the loss parts summed by one thread, each owned pixel of dE/dx written once by one
-thread), so the same image must give the same loss, the same Gram matrices and the same dE/dx
-bit for bit, in either schedule, from the same context or from a fresh one. An evaluation of a
-different image in between leaves other values in the workspace; the result must not depend on
-them (no read of memory the evaluation did not write).
+Every reduction of the path runs in a fixed order (Gram partial tiles reduced by run index, the
+loss parts summed by one thread, each owned pixel of dE/dx written once by one thread), so the
+same image must give the same loss, the same Gram matrices and the same dE/dx bit for bit, in
+either schedule, from the same context or from a fresh one. An evaluation of a different image
+in between leaves other values in the workspace; the result must not depend on them (no read of
+memory the evaluation did not write).
 """
 import numpy as np
 import pytest

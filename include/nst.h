@@ -109,9 +109,10 @@ nst_status nst_content_targets(nst_ctx *ctx, const float *u_dev, int H, int W, v
 nst_status nst_loss_grad(nst_ctx *ctx, const float *x_dev, int H, int W, float *grad_dev,
                          double *loss_dev, void *stream);
 
-/* Same evaluation from host memory: copies x_host to the device, evaluates, copies the gradient
- * and the loss back, and synchronizes the stream before returning. x_host and grad_host should
- * be page-locked for full copy speed. loss_host may be NULL. */
+/* Same evaluation from host memory: copies x_host to the device, evaluates, returns the gradient
+ * and the loss, and synchronizes the stream before returning. x_host should be page-locked for
+ * full copy speed. A page-locked grad_host is written by the evaluation's last kernel directly
+ * (no separate device-to-host copy); any other grad_host receives a copy. loss_host may be NULL. */
 nst_status nst_loss_grad_host(nst_ctx *ctx, const float *x_host, int H, int W, float *grad_host,
                               double *loss_host, void *stream);
 

@@ -1290,10 +1290,23 @@ nst_status nst_loss_grad_host(nst_ctx *ctx, const float *xh, int H, int W, float
     CK(cudaMalloc(&ctx->d_gh, n * sizeof(float)));
     ctx->xh_cap = n;
   }
+  // A page-locked gradient buffer is device-accessible: the last kernel of the evaluation (the
+  // conv1_1 input gradient, one store per owned pixel) writes it over the host link itself, in
+  // place of a separate device-to-host copy after it. (Copy engine and kernel stores move the
+  // same bytes per second over this link; the kernel's own work then hides under its writes.)
+  // Other buffers go through the device copy.
+  float *gdst = ctx->d_gh;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, gh) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) gdst = (float *)pa.devicePointer;
+  } else {
+    cudaGetLastError();   // the query's own error (an unknown pointer), not a pending one
+  }
   CK(cudaMemcpyAsync(ctx->d_xh, xh, n * sizeof(float), cudaMemcpyHostToDevice, s));
-  st = nst_loss_grad(ctx, ctx->d_xh, H, W, ctx->d_gh, ctx->d_loss, stream);
+  st = nst_loss_grad(ctx, ctx->d_xh, H, W, gdst, ctx->d_loss, stream);
   if (st) return st;
-  CK(cudaMemcpyAsync(gh, ctx->d_gh, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (gdst == ctx->d_gh)
+    CK(cudaMemcpyAsync(gh, ctx->d_gh, n * sizeof(float), cudaMemcpyDeviceToHost, s));
   if (lossh) CK(cudaMemcpyAsync(lossh, ctx->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return NST_OK;

@@ -62,3 +62,23 @@ def test_loss_grad_is_bitwise_reproducible(form, sched, H, W, tiles):
     fresh = _ctx(params, u, v, form, SCHEDS[sched], tiles)
     _same(first, _eval(fresh, x))
     fresh.close()
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_host_entry_matches_device_entry(form):
+    """nst_loss_grad_host gives the device call's E and dE/dx bit for bit, with a page-locked
+    gradient buffer (written by the last kernel over the host link) and with a pageable one
+    (device buffer and copy); a stale value in either buffer must not survive."""
+    params, u, v, x = seeded(208, 176, 8)
+    ctx = _ctx(params, u, v, form, native.SCHED_TWO_PASS, (3, 2))
+    ref = _eval(ctx, x)
+    xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    for pinned in (True, False):
+        gh = torch.full(x.shape, 7.0, dtype=torch.float32)
+        if pinned:
+            gh = gh.pin_memory()
+        assert gh.is_pinned() == pinned
+        E = ctx.loss_grad_host(xh.numpy(), gh.numpy())
+        assert E == ref[0], (pinned, E, ref[0])
+        assert np.array_equal(gh.numpy(), ref[1]), pinned
+    ctx.close()

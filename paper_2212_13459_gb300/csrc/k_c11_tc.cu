@@ -77,14 +77,25 @@ __global__ void __launch_bounds__(256) conv11_stage_kernel(const float *__restri
 // same box whose distance is the instruction's LBO. Five instructions per tile: taps (0,1),
 // (2,3), (4,5), (6,7), (8, -) with zero weights in the last one's second half.
 constexpr int kFwdThreads = 192;   // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
-constexpr int kFwdStages = 8;
+constexpr int kFwdStages = 6;
 constexpr int kFwdTH = 16, kFwdTW = 8, kFwdBoxH = kFwdTH + 2, kFwdBoxW = kFwdTW + 2;
 constexpr uint32_t kFwdBoxBytes = kFwdBoxH * kFwdBoxW * 16;   // 2,880
 constexpr uint32_t kFwdStage = 3072;                         // box + zeroed tail
 constexpr uint32_t kFwdB = 16384;                            // 5 x 2 KB used, rest zero
 constexpr uint32_t kFwdOut = 128 * 128;                      // one output tile, 128-B swizzle
 constexpr int kFwdOutBufs = 4;                               // output tiles in flight per CTA
-constexpr size_t kFwdSmem = 1024 + kFwdB + kFwdStages * kFwdStage + kFwdOutBufs * kFwdOut;
+constexpr uint32_t kFwdZero = 8192;                          // zero rows: the Gram's A channels 64..127
+constexpr size_t kFwdSmem =
+    1024 + kFwdB + kFwdStages * kFwdStage + kFwdOutBufs * kFwdOut + kFwdZero;
+static_assert(2 * (kFwdSmem + 1024) <= 228 * 1024, "two conv1_1 CTAs per SM");
+// Gram of the ReLU1_1 output over the owned pixels (Eq. 4), fused: G += T^T T for each owned
+// output tile T (128 pixels x 64 channels, the staged BF16 tile the TMA store reads), on the
+// tensor cores with both operands MN-major in that tile (M = 128 rows of channels, 64..127 read
+// from zero rows, N = 64, K = 16 pixels per instruction, eight instructions a tile), FP32 in
+// TMEM columns 128..191; each CTA writes its 64 x 64 partial (rows of 64 floats, 128-row stride).
+constexpr uint32_t kFwdGramIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                   ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr int kFwdGramRun = 128 * 64;   // floats per CTA partial
 
 __device__ __forceinline__ uint64_t desc_k_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -105,15 +116,17 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
                          const __grid_constant__ CUtensorMap tmO, const float *__restrict__ w11,
                          const float *__restrict__ bias, const BlockGeom *__restrict__ geom,
                          int B, int Hb, int Wb, int tiles_x, int tiles_y,
-                         const int4 *__restrict__ patches, int npatches, unsigned *err) {
+                         const int4 *__restrict__ patches, int npatches,
+                         float *__restrict__ gram_part, unsigned *err) {
   constexpr uint32_t IDESC = idesc_bf16_m128(64);
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kFwdStages], empty_bar[kFwdStages];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2];
+  __shared__ __align__(8) uint64_t gram_bar[kFwdOutBufs], gram_done;   // fused Gram MMAs read
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   __shared__ __align__(16) float bias_sh[64];
-  __shared__ int epi_ok;
+  __shared__ int epi_ok, gram_ok, gram_any, gram_fin;   // broadcasts of single-thread waits
 
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   uint8_t *smem_gen = smem_raw + (smem_base - smem_u32(smem_raw));
@@ -143,6 +156,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       mbar_init(smem_u32(&tfull_bar[i]), 1);
       mbar_init(smem_u32(&tempty_bar[i]), 128);
     }
+    for (int i = 0; i < kFwdOutBufs; i++) mbar_init(smem_u32(&gram_bar[i]), 1);
+    mbar_init(smem_u32(&gram_done), 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -169,9 +184,14 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     *reinterpret_cast<uint4 *>(smem_gen + kFwdB + (size_t)st * kFwdStage + kFwdBoxBytes + k * 16) =
         make_uint4(0u, 0u, 0u, 0u);
   }
+  if (gram_part)   // zero rows after the output tiles: the Gram's A channels 64..127
+    for (int i = threadIdx.x; i < (int)(kFwdZero / 16); i += kFwdThreads)
+      *reinterpret_cast<uint4 *>(smem_gen + o_off + kFwdOutBufs * kFwdOut + (size_t)i * 16) =
+          make_uint4(0u, 0u, 0u, 0u);
   if (threadIdx.x < 64) bias_sh[threadIdx.x] = bias[threadIdx.x];
   fence_proxy_async_smem();
-  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), 128);
+  const uint32_t tmem_cols = gram_part ? 256u : 128u;   // two accumulators (+ the Gram's)
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_base_sh), tmem_cols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -227,14 +247,30 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
     const int q = warp & 3;
     const int row = q * 32 + lane;   // patch pixel (row / 8, row % 8)
     const int et = threadIdx.x - 64;
+    // thread et = 0 issues the stores, et = 32 (the next warp) the fused Gram MMAs; per staging
+    // buffer, whether Gram MMAs reading it are in flight (gpend) and the parity of its next
+    // completion (gph)
+    uint32_t gpend = 0u, gph = 0u;
+    bool gfirst = true;   // no Gram MMA issued yet (the first one overwrites the accumulator)
     int it = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
       const int acc = it & 1;
       const uint32_t use = (uint32_t)(it >> 1);
+      const int ob = it % kFwdOutBufs;
       // one thread waits (bounded) and broadcasts, so all 128 threads leave the loop together;
-      // the same barrier tells everyone that staging tile it % 4 is free again
+      // the same barrier tells everyone that staging tile ob is free again (its store has read
+      // it, see below, and so have the Gram MMAs of its last tile)
       if (et == 0) epi_ok = mbar_wait_sleep(smem_u32(&tfull_bar[acc]), use & 1u, &abort_flag, err);
+      if (et == 32) {
+        gram_ok = 1;
+        if ((gpend >> ob) & 1u) {
+          gram_ok = mbar_wait_sleep(smem_u32(&gram_bar[ob]), (gph >> ob) & 1u, &abort_flag, err);
+          gph ^= 1u << ob;
+          gpend &= ~(1u << ob);
+        }
+      }
       named_bar_sync(1, 128);
+      if (!gram_ok) break;
       if (!epi_ok) break;
       tc_fence_after();
       float v[64];
@@ -248,7 +284,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       const int y = oy + row / kFwdTW, x = ox + row % kFwdTW;
       const BlockGeom g = geom[b];
       const bool valid = y < g.eh && x < g.ew;
-      uint8_t *orow = smem_gen + o_off + (size_t)(it % kFwdOutBufs) * kFwdOut + (size_t)row * 128;
+      uint8_t *orow = smem_gen + o_off + (size_t)ob * kFwdOut + (size_t)row * 128;
 #pragma unroll
       for (int c = 0; c < 8; c++) {
         const float4 b0 = *reinterpret_cast<const float4 *>(bias_sh + c * 8);
@@ -263,20 +299,68 @@ __global__ void __launch_bounds__(kFwdThreads, 2)
       }
       fence_proxy_async_smem();
       named_bar_sync(1, 128);
+      const uint32_t tile = smem_base + o_off + (uint32_t)ob * kFwdOut;
       if (et == 0) {
-        tma_store_4d(&tmO, smem_base + o_off + (uint32_t)(it % kFwdOutBufs) * kFwdOut, 0, ox, oy,
-                     b);
+        tma_store_4d(&tmO, tile, 0, ox, oy, b);
         bulk_commit();
         bulk_wait_read_3();   // the tile written next (it + 1) was stored at it + 1 - 4
       }
+      if (et == 32) {
+        // an owned tile (the patch list's fourth field) adds T^T T to the Gram accumulator: its
+        // 16-pixel row pairs are the K steps, read in place by the tensor cores
+        if (gram_part && patches && __ldg(patches + t).w) {
+          tc_fence_after();
+          const uint32_t zero = smem_base + o_off + kFwdOutBufs * kFwdOut;
+#pragma unroll
+          for (int kk = 0; kk < 8; kk++) {
+            const uint32_t a0 = tile + (uint32_t)kk * 2048u;
+            mma_bf16(tmem_base + 128u, sw128_desc_mn(a0, zero + (uint32_t)(kk & 3) * 2048u - a0),
+                     sw128_desc_mn(a0, kFwdZero), kFwdGramIdesc, gfirst && kk == 0 ? 0u : 1u);
+          }
+          gfirst = false;
+          mma_commit(smem_u32(&gram_bar[ob]));
+          gpend |= 1u << ob;
+        }
+      }
     }
     if (et == 0) bulk_wait_all();
+    if (gram_part) {
+      // this CTA's Gram partial: one commit after the last MMA covers all of them
+      if (et == 32) {
+        int ok = 1;
+        if (!gfirst) {
+          mma_commit(smem_u32(&gram_done));
+          ok = mbar_wait_sleep(smem_u32(&gram_done), 0u, &abort_flag, err);
+        }
+        // (own variables: a thread that left the loop on an abort may not have read epi_ok yet)
+        gram_fin = ok;
+        gram_any = gfirst ? 0 : 1;
+      }
+      named_bar_sync(1, 128);
+      tc_fence_after();
+      if (q < 2) {   // rows = channels 0..63 (TMEM lanes 64..127 hold the zero rows' products)
+        float v[64];
+        if (gram_any && gram_fin) {
+          const uint32_t tg = tmem_base + ((uint32_t)(q * 32) << 16) + 128u;
+          tmem_ld32(tg, v);
+          tmem_ld32(tg + 32, v + 32);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 64; j++) v[j] = 0.f;
+        }
+        float4 *dst = reinterpret_cast<float4 *>(gram_part + (size_t)blockIdx.x * kFwdGramRun +
+                                                 (size_t)row * 64);
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+          dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, 128);
+    tmem_dealloc(tmem_base, tmem_cols);
   }
 }
 
@@ -478,7 +562,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w11,
                                  const float *bias, const BlockGeom *geom, int B, int Hb, int Wb,
                                  void *stage_buf, __nv_bfloat16 *out, const int4 *patches,
-                                 int npatches, unsigned *err, cudaStream_t s) {
+                                 int npatches, float *gram_part, int *gram_runs, unsigned *err,
+                                 cudaStream_t s) {
+  if (gram_runs) *gram_runs = 0;
+  if (gram_part && (!patches || !gram_runs)) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(conv11_fwd_tc_kernel,
@@ -516,10 +603,14 @@ cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w1
   const int tiles_x = (Wb + kFwdTW - 1) / kFwdTW, tiles_y = (Hb + kFwdTH - 1) / kFwdTH;
   const long long ntiles = patches ? npatches : (long long)B * tiles_x * tiles_y;
   if (ntiles <= 0) return cudaSuccess;
-  const int grid = (int)std::min<long long>(ntiles, 2LL * tc_num_sms());
+  // with the Gram, always two CTAs per SM: CTA c sums the owned patches c, c + grid, ... (the
+  // list puts them first), a split that depends on the owned patches alone
+  const int grid = gram_part ? 2 * tc_num_sms()
+                             : (int)std::min<long long>(ntiles, 2LL * tc_num_sms());
   conv11_fwd_tc_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(m, mo, w11, bias, geom, B, Hb, Wb,
                                                            tiles_x, tiles_y, patches,
-                                                           (int)ntiles, err);
+                                                           (int)ntiles, gram_part, err);
+  if (gram_runs) *gram_runs = gram_part ? grid : 0;
   return cudaGetLastError();
 }
 

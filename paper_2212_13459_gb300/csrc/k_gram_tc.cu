@@ -302,16 +302,22 @@ cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStr
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  return launch_gram_tc_reduce(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc, s);
+}
+
+cudaError_t launch_gram_tc_reduce(const float *part, int nruns, int C, int N, int nI, int nJ,
+                                  double *Gacc, cudaStream_t s) {
+  if (nruns <= 0) return cudaSuccess;
   // float4 lanes where that still gives two CTAs per SM; otherwise one element per lane and 16
   // warps per CTA splitting the runs (C = 64, 128: few elements, several hundred runs)
-  const long long n = (long long)a.C * a.C;
+  const long long n = (long long)C * C;
   const int sms = tc_num_sms();
   if (n / 128 >= 2LL * sms) {
     const int grid = (int)std::min<long long>(n / 128, 8LL * sms);
-    gram_tc_reduce_kernel<4, 8><<<grid, 256, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
+    gram_tc_reduce_kernel<4, 8><<<grid, 256, 0, s>>>(part, nruns, C, N, nI, nJ, Gacc);
   } else {
     const int grid = (int)std::min<long long>(n / 32, 4LL * sms);
-    gram_tc_reduce_kernel<1, 16><<<grid, 512, 0, s>>>(a.part, nruns, a.C, a.N, a.nI, a.nJ, Gacc);
+    gram_tc_reduce_kernel<1, 16><<<grid, 512, 0, s>>>(part, nruns, C, N, nI, nJ, Gacc);
   }
   return cudaGetLastError();
 }

@@ -187,6 +187,10 @@ struct nst_ctx {
   double *d_cpart = nullptr;
   size_t cpart_cap = 0;
   float *d_gpart = nullptr;
+  // the ReLU1_1 Gram partials the conv1_1 forward writes (one 128 x 64 tile per CTA) and their
+  // count for the batch's Gram reduction (0: that forward took no Gram)
+  float *d_g11part = nullptr;
+  int g11_runs = 0;
   size_t gpart_cap = 0;
   unsigned *d_err = nullptr;
   // mean / std terms (Eq. 5)
@@ -534,13 +538,30 @@ nst_status build_plan(nst_ctx *ctx, int H, int W, int margin, PassPlan **out) {
       // conv1_1 (its own kernel, 16 x 8 patches)
       PatchList &c11 = bt.fwd[k][0];
       c11 = PatchList{(int)patches.size(), 0, 16, 8};
+      // Passes that take the Grams (Step 1, the style targets, the resident pass): the patch
+      // grid sits on multiples of 16 x 8 px of the block buffer, as do the owned rectangle's
+      // edges (block bounds and margins are multiples of 16 px; at the image edge the owned
+      // rectangle ends with the valid extent, past which the activation is zero), so every
+      // patch is wholly owned or wholly not, and the fused ReLU1_1 Gram takes whole patches:
+      // the fourth field flags the patches that meet the owned rectangle. The owned patches
+      // come first, block by block in row order: the same image positions in the same order
+      // under either margin, so the kernel's fixed split of them over its CTAs (and the FP32
+      // order of each CTA's sum) does not depend on the pass.
+      const bool gram = k != kFwdContent;
+      std::vector<int4> rest;
       for (int j = 0; j < bt.B; j++) {
         const Tile &t = p.tiles[bt.t0 + j];
         const Iv ry = local_rect(ny[bt.t0 + j].F[k][0], t.ey0, t.ey1 - t.ey0, p.Hb, false);
         const Iv rx = local_rect(nx[bt.t0 + j].F[k][0], t.ex0, t.ex1 - t.ex0, p.Wb, false);
-        for (int y = ry.a; y < ry.b; y += 16)
-          for (int x = rx.a; x < rx.b; x += 8) patches.push_back(make_int4(j, y, x, 0));
+        const OwnRect &o = own[bt.t0 + j];   // style layer 0 (ReLU1_1), level 0
+        const int ya = gram ? ry.a / 16 * 16 : ry.a, xa = gram ? rx.a / 8 * 8 : rx.a;
+        for (int y = ya; y < ry.b; y += 16)
+          for (int x = xa; x < rx.b; x += 8) {
+            const bool op = gram && y < o.y1 && y + 16 > o.y0 && x < o.x1 && x + 8 > o.x0;
+            (op ? patches : rest).push_back(make_int4(j, y, x, op ? 1 : 0));
+          }
       }
+      patches.insert(patches.end(), rest.begin(), rest.end());
       c11.n = (int)patches.size() - c11.off;
     }
     for (int k = 0; k < kFwdKinds; k++)
@@ -685,8 +706,15 @@ nst_status run_conv(nst_ctx *ctx, ConvArgs a, cudaStream_t s) {
 
 template <typename T>
 nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const Workspace &ws,
-                         const float *img, int last_conv, bool for_backward, cudaStream_t s) {
+                         const float *img, int last_conv, bool for_backward, cudaStream_t s,
+                         bool grams = false) {
   const BlockGeom *geom = p.d_geom + bt.t0;
+  ctx->g11_runs = 0;
+  // grams: gram_batch follows; on the tensor cores the conv1_1 forward also takes the ReLU1_1
+  // Gram of its owned patches (partials reduced there)
+  const bool fuse_g11 = grams && ctx->use_tc;
+  if (fuse_g11 && !ctx->d_g11part)
+    CK(cudaMalloc(&ctx->d_g11part, (size_t)2 * tc_num_sms() * 128 * 64 * sizeof(float)));
   {
     Timer tm(ctx, kTOther, s);
     ctx->launches += ctx->use_tc ? 2 : 1;   // tensor-core form: staging + convolution
@@ -696,7 +724,9 @@ nst_status forward_batch(nst_ctx *ctx, const PassPlan &p, const Batch &bt, const
                                   : (for_backward ? kFwdStep2 : kFwdStats)][0];
       cudaError_t e = launch_conv11_fwd_tc(img, p.H, p.W, ctx->d_w11, ctx->d_bias[0], geom, bt.B,
                                            p.Hb, p.Wb, ws.g[1], (__nv_bfloat16 *)ws.act[0],
-                                           p.d_patches + pl.off, pl.n, ctx->d_err, s);
+                                           p.d_patches + pl.off, pl.n,
+                                           fuse_g11 ? ctx->d_g11part : nullptr, &ctx->g11_runs,
+                                           ctx->d_err, s);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "conv1_1 tensor-core forward launch");
     } else {
       launch_conv11_fwd<T>(img, p.H, p.W, ctx->h_c11, geom, bt.B, p.Hb, p.Wb, (T *)ws.act[0], s);
@@ -783,6 +813,13 @@ nst_status gram_batch(nst_ctx *ctx, PassPlan &p, const Batch &bt, const Workspac
     const int l = kStyleConv[si], lv = kLevel[l];
     Timer tm(ctx, kTGram, s);
     ctx->launches += 2;
+    if (ctx->use_tc && si == 0 && ctx->g11_runs > 0) {
+      // ReLU1_1: the conv1_1 forward took the Gram of its owned patches; reduce its partials
+      cudaError_t e = launch_gram_tc_reduce(ctx->d_g11part, ctx->g11_runs, 64, 64, 1, 1,
+                                            ctx->d_gacc + gram_offset(0), s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "ReLU1_1 Gram reduction launch");
+      continue;
+    }
     if (ctx->use_tc) {
       GramTcArgs a{};
       a.maps = p.d_maps + (size_t)si * nt + bt.t0;
@@ -909,7 +946,7 @@ nst_status stats_pass(nst_ctx *ctx, const float *img, int H, int W, PassKind kin
   const int nt = (int)p->tiles.size();
   for (const Batch &bt : p->batches) {
     const int last = kind == kPassContentTarget ? kContentConv : kNConv - 1;
-    st = forward_batch<T>(ctx, *p, bt, ws, img, last, false, s);
+    st = forward_batch<T>(ctx, *p, bt, ws, img, last, false, s, kind == kPassStyleStats);
     if (st) return st;
     if (kind == kPassStyleStats) {
       st = gram_batch<T>(ctx, *p, bt, ws, s, moments);
@@ -949,7 +986,7 @@ nst_status loss_grad_impl(nst_ctx *ctx, const float *x, float *grad, double *los
   ctx->pass_batches = (int)p->batches.size();
   if (resident) {
     const Batch &bt = p->batches[0];
-    st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, true, s);
+    st = forward_batch<T>(ctx, *p, bt, ws, x, kNConv - 1, true, s, true);
     if (st) return st;
     st = gram_batch<T>(ctx, *p, bt, ws, s, ctx->aug);
     if (st) return st;
@@ -1183,7 +1220,7 @@ nst_status nst_destroy(nst_ctx *ctx) {
   }
   cudaFree(ctx->d_ghat); cudaFree(ctx->d_ctgt); cudaFree(ctx->d_gacc); cudaFree(ctx->d_gx);
   cudaFree(ctx->d_R); cudaFree(ctx->d_parts); cudaFree(ctx->d_loss); cudaFree(ctx->d_cpart);
-  cudaFree(ctx->d_gpart); cudaFree(ctx->d_err); cudaFree(ctx->d_ws);
+  cudaFree(ctx->d_gpart); cudaFree(ctx->d_g11part); cudaFree(ctx->d_err); cudaFree(ctx->d_ws);
   cudaFree(ctx->d_xh); cudaFree(ctx->d_gh);
   cudaFree(ctx->d_sacc); cudaFree(ctx->d_mu); cudaFree(ctx->d_sigma); cudaFree(ctx->d_alpha);
   cudaFree(ctx->d_cspart);

@@ -110,13 +110,18 @@ cudaError_t launch_timeout_check(long long limit_cycles, unsigned *err, cudaStre
 // relu(bias + conv1_1(block image)) inside each block's valid extent, zero elsewhere; w11 is
 // [64][3][3][3] FP32 holding BF16 values; stage_buf (16 bytes per buffer pixel, 16-byte aligned)
 // receives the staged block images; patches (optional, npatches 16 x 8 output patches
-// {block, y0, x0, 0}) restricts the convolution to them. Input gradient:
+// {block, y0, x0, owned}) restricts the convolution to them. gram_part (optional, needs patches):
+// the Gram sum_p V_p V_p^T over the patches with owned != 0 (each wholly inside its block's owned
+// rectangle, or past the valid extent, where V = 0) is accumulated per CTA on the tensor cores
+// and written as *gram_runs partials of 128 x 64 floats (rows 0..63 used), the layout
+// launch_gram_tc_reduce reads (C = N = 64, one tile). Input gradient:
 // grad[ci][ey0 + y][ex0 + x] for the owned (inner) pixels of every block, from the gated
 // ReLU1_1 gradient g [B][Hb][Wb][64].
 cudaError_t launch_conv11_fwd_tc(const float *img, int H, int W, const float *w11,
                                  const float *bias, const BlockGeom *geom, int B, int Hb, int Wb,
                                  void *stage_buf, __nv_bfloat16 *out, const int4 *patches,
-                                 int npatches, unsigned *err, cudaStream_t s);
+                                 int npatches, float *gram_part, int *gram_runs, unsigned *err,
+                                 cudaStream_t s);
 cudaError_t launch_conv11_dgrad_tc(const __nv_bfloat16 *g, const float *w11,
                                    const BlockGeom *geom, const OwnRect *inner, int B, int Hb,
                                    int Wb, int max_inner_h, int max_inner_w, float *grad, int H,
@@ -138,6 +143,10 @@ void gram_tc_patch(int own_h, int own_w, int *TH, int *TW);
 cudaError_t encode_gram_map(CUtensorMap *m, const void *base, int C, int own_w, int own_h,
                             long long row_stride_px, int TH, int TW);
 cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStream_t s);
+// Gacc[i][j] += the sum over nruns FP32 partial tiles (run r at part + r * nI * nJ * 128 * N,
+// tile (I, J) of 128 x N floats), fixed order; the reduction launch_gram_tc ends with.
+cudaError_t launch_gram_tc_reduce(const float *part, int nruns, int C, int N, int nI, int nJ,
+                                  double *Gacc, cudaStream_t s);
 
 // Chunking of a flat [npix][C] feature matrix for the CUDA-core Gram kernels: about 1,216 CTAs
 // over the 64 x 64 block pairs (npairs = nb (nb + 1) / 2, nb = C / 64), chunks of a multiple of

@@ -23,14 +23,30 @@ namespace {
 using namespace nst::tc;
 
 constexpr int kThreads = 192;
-constexpr int kStages = 4;
 constexpr uint32_t kSlab = 64 * 128;  // one 64-pixel x 64-channel BF16 slab
+constexpr uint32_t kSmemMax = 227 * 1024;
 
-template <int N>
+// Stages of the box ring: ALOAD (some I tile's channels lie outside the J tile, C = 512) keeps
+// room for two A slabs per stage, 4 stages; otherwise A is always read from the B slabs (or the
+// zero slab) and a stage is the B slabs alone, so more boxes are in flight (8 at N = 64, 128;
+// 6 at N = 256).
+template <int N, bool ALOAD>
+struct GramCfg {
+  static constexpr uint32_t A_BYTES = ALOAD ? 2 * kSlab : 0u;
+  static constexpr uint32_t B_BYTES = (N / 64) * kSlab;
+  static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int FIT = (int)((kSmemMax - kSlab - 1024) / STAGE_BYTES);
+  static constexpr int STAGES = ALOAD ? 4 : (FIT > 8 ? 8 : FIT);
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + kSlab + 1024;
+};
+
+template <int N, bool ALOAD>
 __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
-  constexpr uint32_t A_BYTES = 2 * kSlab;
-  constexpr uint32_t B_BYTES = (N / 64) * kSlab;
-  constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+  using Cfg = GramCfg<N, ALOAD>;
+  constexpr int kStages = Cfg::STAGES;
+  constexpr uint32_t A_BYTES = Cfg::A_BYTES;
+  constexpr uint32_t B_BYTES = Cfg::B_BYTES;
+  constexpr uint32_t STAGE_BYTES = Cfg::STAGE_BYTES;
   constexpr uint32_t ZERO_OFF = kStages * STAGE_BYTES;   // one slab of zeros after the stages
   constexpr uint32_t TMEM_COLS = N;
   // kind::f16, FP32 D, BF16 A/B, both MN-major, M = 128, N
@@ -58,7 +74,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
     else if (c0 >= J * N && c0 + 64 <= J * N + N) a_src[sl] = (c0 - J * N) / 64;   // B slab
     else { a_src[sl] = -1; a_load = true; }                          // own A slab
   }
-  const uint32_t tx_bytes = B_BYTES + (a_load ? A_BYTES : 0u);
+  // (without room for A slabs (ALOAD false) the host has checked that no tile needs them)
+  const uint32_t tx_bytes = B_BYTES + (ALOAD && a_load ? A_BYTES : 0u);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) {
@@ -91,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_tc_kernel(GramTcArgs a) {
         const uint32_t sa = smem_base + stage * STAGE_BYTES, sb = sa + A_BYTES;
         const int x = (k % ch.nbx) * a.TW, y = (k / ch.nbx) * a.TH;
         mbar_expect_tx(fb, tx_bytes);
-        if (a_load) {
+        if (ALOAD && a_load) {
           tma_load_4d(sa, map, fb, I * 128, x, y, 0);
           tma_load_4d(sa + kSlab, map, fb, I * 128 + 64, x, y, 0);
         }
@@ -239,18 +256,31 @@ __global__ void __launch_bounds__(NW * 32) gram_tc_reduce_kernel(const float *__
   }
 }
 
-template <int N>
+template <int N, bool ALOAD>
 cudaError_t launch_n(const GramTcArgs &a, int nruns, cudaStream_t s) {
-  constexpr size_t smem = (size_t)kStages * (2 * kSlab + (N / 64) * kSlab) + kSlab + 1024;
+  constexpr size_t smem = GramCfg<N, ALOAD>::SMEM;
+  static_assert(smem <= kSmemMax, "Gram kernel shared memory");
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<N>,
+    cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<N, ALOAD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  gram_tc_kernel<N><<<dim3(nruns, a.nI * a.nJ), kThreads, smem, s>>>(a);
+  gram_tc_kernel<N, ALOAD><<<dim3(nruns, a.nI * a.nJ), kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// whether some (I, J) tile reads A slabs of its own: an I-tile slab below C that lies outside
+// the J tile (the same test the kernel makes per tile)
+bool gram_needs_aload(const GramTcArgs &a) {
+  for (int I = 0; I < a.nI; I++)
+    for (int J = 0; J < a.nJ; J++)
+      for (int sl = 0; sl < 2; sl++) {
+        const int c0 = I * 128 + 64 * sl;
+        if (c0 < a.C && !(c0 >= J * a.N && c0 + 64 <= J * a.N + a.N)) return true;
+      }
+  return false;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -295,10 +325,11 @@ cudaError_t encode_gram_map(CUtensorMap *m, const void *base, int C, int own_w, 
 cudaError_t launch_gram_tc(const GramTcArgs &a, int nruns, double *Gacc, cudaStream_t s) {
   if (nruns <= 0) return cudaSuccess;
   cudaError_t e;
+  const bool aload = gram_needs_aload(a);
   switch (a.N) {
-    case 64: e = launch_n<64>(a, nruns, s); break;
-    case 128: e = launch_n<128>(a, nruns, s); break;
-    case 256: e = launch_n<256>(a, nruns, s); break;
+    case 64: e = aload ? launch_n<64, true>(a, nruns, s) : launch_n<64, false>(a, nruns, s); break;
+    case 128: e = aload ? launch_n<128, true>(a, nruns, s) : launch_n<128, false>(a, nruns, s); break;
+    case 256: e = aload ? launch_n<256, true>(a, nruns, s) : launch_n<256, false>(a, nruns, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;

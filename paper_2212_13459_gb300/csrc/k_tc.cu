@@ -549,6 +549,10 @@ constexpr int kHaloTH = 16, kHaloTW = 8, kHaloBoxW = kHaloTW + 2, kHaloBoxH = kH
 constexpr uint32_t kHaloBoxBytes = kHaloBoxW * kHaloBoxH * 128;        // 23,040
 constexpr uint32_t kHaloStage = (kHaloBoxBytes + 1023u) & ~1023u;      // 23,552
 constexpr uint32_t kHaloSmemMax = 227 * 1024;
+// the fused input-gradient form (MASK_SMEM): main-phase boxes in kMaskAStages stages, the tile's
+// own 16 x 8 phase-2 box (16 KB) in a ring of kMaskVStages
+constexpr int kMaskAStages = 3, kMaskVStages = 4;
+constexpr uint32_t kMaskVStage = 128 * 128;
 
 template <int BN, int KB, int P2KB, int NT>
 struct HaloCfg {
@@ -578,29 +582,38 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr uint32_t IDESC = make_idesc(BN);
   constexpr int KBT = KB + P2KB;   // K-blocks per tile
   // MASK_SMEM: the phase-2 K-block is the fused V R term of an input gradient whose ReLU mask
-  // is that same activation V; the epilogue reads the mask from the K-block's box, which covers
-  // the tile plus a one-pixel border, and the box's stage is released by the epilogue warps,
-  // not by the MMA. Each tile's phase-2 box lands in an odd stage.
-  static_assert(!MASK_SMEM || (KB == 1 && P2KB == 1 && STAGES % 2 == 0 && NT == 1 && BN == 64),
+  // is that same activation V. Its box is the tile's own 16 x 8 pixels (the V R term reads the
+  // centre tap only, the mask the pixel itself): 16 KB in a ring of its own (SV stages), read by
+  // the MMAs and then by the epilogue, whose warps release it; the main-phase boxes keep SA
+  // stages, released by the MMA.
+  static_assert(!MASK_SMEM || (KB == 1 && P2KB == 1 && NT == 1 && BN == 64),
                 "mask from the phase-2 box");
+  constexpr int SA = MASK_SMEM ? kMaskAStages : STAGES;
+  constexpr int SV = MASK_SMEM ? kMaskVStages : 1;
 
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], w_bar;
+  __shared__ __align__(8) uint64_t vfull_bar[SV], vempty_bar[SV];
   __shared__ __align__(8) uint64_t tfull_bar[NACC], tempty_bar[NACC];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
   const uint32_t smem_base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   const uint32_t w_base = smem_base, a_base = smem_base + Cfg::W_BYTES;
+  const uint32_t v_base = a_base + SA * kHaloStage;   // (MASK_SMEM) the phase-2 ring
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // this CTA's N slice, and its share of the M tiles
   const int nt = blockIdx.x % NT, m_first = blockIdx.x / NT, m_step = gridDim.x / NT;
   const int m_total = tg.total;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; s++) {
+    for (int s = 0; s < SA; s++) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), MASK_SMEM && (s & 1) ? kEpiThreads / 32 : 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int s = 0; s < SV; s++) {
+      mbar_init(smem_u32(&vfull_bar[s]), 1);
+      mbar_init(smem_u32(&vempty_bar[s]), kEpiThreads / 32);
     }
     mbar_init(smem_u32(&w_bar), 1);
     for (int i = 0; i < NACC; i++) {
@@ -628,13 +641,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                       nt * BN);
       for (int cb = 0; cb < P2KB; cb++)
         tma_load_2d(w_base + (9 * KB + cb) * Cfg::TILE_B, &tmB2, wb, cb * kBK, nt * BN);
-      int stage = 0;
-      uint32_t phase = 0;
+      int stage = 0, vst = 0;
+      uint32_t phase = 0, vph = 0;
       bool ok = true;
       for (int t = m_first; t < m_total && ok; t += m_step) {
         int b, oy, ox;
         patch_origin(a, tg, t, b, oy, ox);
         for (int kb = 0; kb < KBT; kb++) {
+          if (MASK_SMEM && kb == KB) {   // the tile's own pixels of V (no halo)
+            if (!mbar_wait(smem_u32(&vempty_bar[vst]), vph ^ 1, &abort_flag, a.err)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = smem_u32(&vfull_bar[vst]);
+            mbar_expect_tx(fb, kMaskVStage);
+            tma_load_4d(v_base + vst * kMaskVStage, &tmA2, fb, 0, ox, oy, b);
+            if (++vst == SV) { vst = 0; vph ^= 1; }
+            continue;
+          }
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, &abort_flag, a.err)) {
             ok = false;
             break;
@@ -646,7 +670,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_4d(sa, &tmA, fb, kb * kBK, ox - 1, oy - 1, b);
           else
             tma_load_4d(sa, &tmA2, fb, (kb - KB) * kBK, ox - 1, oy - 1, b);
-          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+          if (++stage == SA) { stage = 0; phase ^= 1; }
         }
       }
     }
@@ -654,11 +678,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     // The whole warp runs the issue loop (its waits and loop control are warp-uniform), and one
     // elected lane issues each K-block's MMAs and commit: a loop run by a single lane issues
     // several times slower once epilogue warps keep this warp's scheduler busy, and a 64-wide
-    // MMA takes only 48 cycles. (The 256-wide MMAs of the other kernels take 128 cycles; there the single-lane
-    // loop keeps up and measured slightly faster.)
+    // MMA takes only 48 cycles. (The 256-wide MMAs of the other kernels take 128 cycles; there
+    // the single-lane loop keeps up and measured slightly faster.)
     bool ok = mbar_wait_warp(smem_u32(&w_bar), 0, &abort_flag, a.err);
-    int stage = 0;
-    uint32_t phase = 0;
+    int stage = 0, vst = 0;
+    uint32_t phase = 0, vph = 0;
     int it = 0;
     for (int t = m_first; t < m_total && ok; t += m_step, it++) {
       const int acc = it % NACC;
@@ -667,6 +691,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const uint32_t d = tmem_base + (uint32_t)(acc * BN);
       for (int kb = 0; kb < KBT; kb++) {
+        if (MASK_SMEM && kb == KB) {   // V R from the tile's own 16 x 8 box (no commit: the
+          // epilogue reads the mask from it and releases the stage)
+          if (!mbar_wait_warp(smem_u32(&vfull_bar[vst]), vph, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (elect_one()) {
+            const uint64_t da = sw128_desc(v_base + vst * kMaskVStage);
+            const uint64_t db = sw128_desc(w_base + 9 * KB * Cfg::TILE_B);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; k++)
+              mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, 1u);
+          }
+          __syncwarp();
+          if (++vst == SV) { vst = 0; vph ^= 1; }
+          continue;
+        }
         if (!mbar_wait_warp(smem_u32(&full_bar[stage]), phase, &abort_flag, a.err)) {
           ok = false;
           break;
@@ -698,11 +740,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int k = 0; k < kBK / 16; k++)
               mma_bf16(d, da + (uint64_t)(k * 2), db + (uint64_t)(k * 2), IDESC, 1u);
           }
-          if (!(MASK_SMEM && kb == KB))   // (that box is released by the epilogue)
-            mma_commit(smem_u32(&empty_bar[stage]));
+          mma_commit(smem_u32(&empty_bar[stage]));
         }
         __syncwarp();
-        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        if (++stage == SA) { stage = 0; phase ^= 1; }
       }
       if (!ok) break;
       if (elect_one()) mma_commit(smem_u32(&tfull_bar[acc]));
@@ -727,23 +768,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool inb = y < a.Hb && x < a.Wb;
       const BlockGeom g = a.geom[b];
       const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-      // the ReLU mask from the tile's phase-2 box (this pixel's row: box pixel (y + 1, x + 1));
+      // the ReLU mask from the tile's phase-2 box (this pixel's row: box pixel = patch pixel);
       // its full barrier completed before the MMAs that the accumulator waited for, and waiting
       // on it here acquires the TMA's writes
       const uint8_t *mrow = nullptr;
       int mswz = 0, ms = 0;
       if constexpr (MASK_SMEM) {
-        const int gk = it * KBT + KB;
-        ms = gk % STAGES;
+        ms = it % SV;
         int mok = 0;
         if (lane == 0)
-          mok = mbar_wait_sleep(smem_u32(&full_bar[ms]), (uint32_t)(gk / STAGES) & 1u,
-                                &abort_flag, a.err);
+          mok = mbar_wait_sleep(smem_u32(&vfull_bar[ms]), (uint32_t)(it / SV) & 1u, &abort_flag,
+                                a.err);
         if (!__shfl_sync(0xffffffffu, mok, 0)) break;
-        const int pbox = (row / kHaloTW + 1) * kHaloBoxW + row % kHaloTW + 1;
-        mrow = smem_raw + (a_base - smem_u32(smem_raw)) + (size_t)ms * kHaloStage +
-               (size_t)pbox * 128;
-        mswz = pbox & 7;
+        mrow = smem_raw + (v_base - smem_u32(smem_raw)) + (size_t)ms * kMaskVStage +
+               (size_t)row * 128;
+        mswz = row & 7;
       }
       if (a.pool_out) {
         // pooled forward: two 16-lane reads of the 16x256b layout (pixel-row pairs 4q, 4q + 2)
@@ -765,7 +804,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(smem_u32(&tempty_bar[acc]));
       if constexpr (MASK_SMEM) {   // every lane has read its mask row: release the box's stage
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty_bar[ms]));
+        if (lane == 0) mbar_arrive(smem_u32(&vempty_bar[ms]));
       }
     }
   }
@@ -1271,13 +1310,16 @@ template <int BN, int KB, int P2KB, int NT, bool MASK_SMEM = false>
 cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtensorMap &A2,
                         const CUtensorMap &B2, const ConvArgs &a, cudaStream_t s) {
   using Cfg = HaloCfg<BN, KB, P2KB, NT>;
+  // (MASK_SMEM: the main-phase ring and the 16 x 8 phase-2 ring)
+  constexpr size_t smem = MASK_SMEM ? 1024 + Cfg::W_BYTES + (size_t)kMaskAStages * kHaloStage +
+                                          (size_t)kMaskVStages * kMaskVStage
+                                    : Cfg::SMEM;
   static_assert(Cfg::STAGES >= 2, "halo kernel needs two activation stages");
-  static_assert(Cfg::SMEM <= kHaloSmemMax, "halo kernel shared memory");
+  static_assert(smem <= kHaloSmemMax, "halo kernel shared memory");
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, KB, P2KB, NT, MASK_SMEM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -1292,8 +1334,8 @@ cudaError_t launch_halo(const CUtensorMap &A, const CUtensorMap &B, const CUtens
   if (tg.total <= 0) return cudaSuccess;
   int grid = std::min(tg.total * NT, g_num_sms);
   grid = std::max(NT, grid / NT * NT);
-  conv_tc_halo_kernel<BN, KB, P2KB, NT, MASK_SMEM><<<grid, kThreads, Cfg::SMEM, s>>>(A, B, A2, B2,
-                                                                                  a, tg);
+  conv_tc_halo_kernel<BN, KB, P2KB, NT, MASK_SMEM><<<grid, kThreads, smem, s>>>(A, B, A2, B2, a,
+                                                                             tg);
   return cudaGetLastError();
 }
 
@@ -1375,8 +1417,14 @@ cudaError_t launch_conv_tc_halo(const ConvArgs &a, int BN, int KB, int P2KB, int
   cudaError_t e;
   if ((e = encode_act_halo(&mA, a.A, a.B, a.Hb, a.Wb, a.cin)) != cudaSuccess) return e;
   if ((e = encode_wt(&mB, a.Wt, a.cout, 9 * a.cin, BN)) != cudaSuccess) return e;
+  // the ReLU mask of an input gradient is usually the V of its fused V R term: the kernel then
+  // loads that phase as the tile's own 16 x 8 box and reads the mask from it
+  const bool mask_smem =
+      BN == 64 && KB == 1 && P2KB == 1 && NT == 1 && a.mask == a.A2 && a.k2 == a.cout;
   if (a.k2) {
-    if ((e = encode_act_halo(&mA2, a.A2, a.B, a.Hb, a.Wb, a.k2)) != cudaSuccess) return e;
+    e = mask_smem ? encode_act(&mA2, a.A2, a.B, a.Hb, a.Wb, a.k2, kHaloTH, kHaloTW)
+                  : encode_act_halo(&mA2, a.A2, a.B, a.Hb, a.Wb, a.k2);
+    if (e != cudaSuccess) return e;
     if ((e = encode_wt(&mB2, a.W2, a.cout, a.k2, BN)) != cudaSuccess) return e;
   } else {
     mA2 = mA;
@@ -1384,9 +1432,7 @@ cudaError_t launch_conv_tc_halo(const ConvArgs &a, int BN, int KB, int P2KB, int
   }
   if (BN == 64 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<64, 1, 0, 1>(mA, mB, mA2, mB2, a, s);
   if (BN == 64 && KB == 1 && P2KB == 1 && NT == 1) {
-    // the ReLU mask of an input gradient is usually the V of its fused V R term: read it from
-    // the phase-2 box then
-    if (a.mask == a.A2 && a.k2 == a.cout) return launch_halo<64, 1, 1, 1, true>(mA, mB, mA2, mB2, a, s);
+    if (mask_smem) return launch_halo<64, 1, 1, 1, true>(mA, mB, mA2, mB2, a, s);
     return launch_halo<64, 1, 1, 1>(mA, mB, mA2, mB2, a, s);
   }
   if (BN == 128 && KB == 1 && P2KB == 0 && NT == 1) return launch_halo<128, 1, 0, 1>(mA, mB, mA2, mB2, a, s);

@@ -8,7 +8,9 @@
 //    enters within 2^-17 |x| of its FP32 value; then D[p][n] = sum_k A[p][k] B[n][k] over a
 //    16 x 8 output patch with K = 9 taps x 8, every tap a shifted view of one TMA halo box (see
 //    the kernel). The epilogue adds the bias, applies ReLU, zeroes pixels outside the block's
-//    valid extent and stores the BF16 row.
+//    valid extent and stores the BF16 row. In the passes that take the Gram statistics it also
+//    adds T^T T of every owned output tile T to a per-CTA ReLU1_1 Gram (Eq. 4), on the tensor
+//    cores from the tile it stages for the store (see kFwdGramIdesc).
 //  * input gradient (last line of Algorithm 1): P[q][j] = sum_co g[q][co] Wt[j][co] with
 //    j = 3 tap + ci (27 of N = 32 columns), over an 18 x 14 box of the gated ReLU1_1 gradient
 //    loaded by TMA (zero outside the buffer); the epilogue forms

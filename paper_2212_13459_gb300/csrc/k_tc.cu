@@ -196,8 +196,9 @@ __device__ __forceinline__ uint32_t pool_nibble_shift(int k) { return 8 * (k & 3
 // (exchanges with t ^ 2, then t ^ 1, each passing on the words the partner keeps) and over the
 // window's two columns (t ^ 4): 4 shuffles where an OR of all four words at every thread takes 12.
 // (Reading both 16-lane halves behind one wait and interleaving them measured 6-7 % slower.)
+// pb[k]: the bias of channels n + 8k + 2(t % 4), +1 (loaded once per warp, see the kernel)
 __device__ __forceinline__ void halo_pool16(const ConvArgs &a, const BlockGeom &g, int b, int py0,
-                                            int px0, int n, uint32_t taddr) {
+                                            int px0, int n, uint32_t taddr, const float2 *pb) {
   const int t = threadIdx.x & 31, j = t & 3, c = t >> 2;   // j: channel pair, c: patch column
   float v[16];
   tmem_ld16x256b_x4(taddr, v);
@@ -207,7 +208,7 @@ __device__ __forceinline__ void halo_pool16(const ConvArgs &a, const BlockGeom &
   float m[8];
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    const float2 bb = __ldg(reinterpret_cast<const float2 *>(a.bias + n + 8 * k + 2 * j));
+    const float2 bb = pb[k];
 #pragma unroll
     for (int e = 0; e < 2; e++) {
       const float bias = e ? bb.y : bb.x;
@@ -752,6 +753,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     const int row = q * 32 + lane;
+    // pooled forward (BN = 64: one 32-channel chunk per warp): the bias pairs this thread
+    // applies on every tile, loaded once
+    float2 pbias[4] = {};
+    if (a.pool_out && BN == 64)
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        pbias[k] = __ldg(reinterpret_cast<const float2 *>(a.bias + nt * BN + half * (BN / 2) +
+                                                          8 * k + 2 * (lane & 3)));
     int it = 0;
     for (int t = m_first; t < m_total; t += m_step, it++) {
       const int acc = it % NACC;
@@ -787,11 +796,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (a.pool_out) {
         // pooled forward: two 16-lane reads of the 16x256b layout (pixel-row pairs 4q, 4q + 2)
 #pragma unroll 1
-        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32)
+        for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {
+          float2 pb[4];   // (other widths: this chunk's bias pairs)
+          const float2 *bp = pbias;
+          if constexpr (BN != 64) {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+              pb[k] = __ldg(reinterpret_cast<const float2 *>(a.bias + nt * BN + c + 8 * k +
+                                                             2 * (lane & 3)));
+            bp = pb;
+          }
 #pragma unroll
           for (int grp = 0; grp < 2; grp++)
             halo_pool16(a, g, b, oy + 4 * q + 2 * grp, ox, nt * BN + c,
-                        tbase + ((uint32_t)(16 * grp) << 16) + (uint32_t)c);
+                        tbase + ((uint32_t)(16 * grp) << 16) + (uint32_t)c, bp);
+        }
       } else {
 #pragma unroll 1
         for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 32) {

@@ -278,15 +278,28 @@ __device__ __forceinline__ void swap_tile_read8(const uint8_t *tsm, int j, int c
   r[4] = f1.x; r[5] = f1.y; r[6] = f1.z; r[7] = f1.w;
 }
 
-// epilogue32 for 8 channels n .. n+7 of one pixel
+// 8 consecutive FP32 biases (16-byte aligned)
+__device__ __forceinline__ void load8_bias(const float *p, float *bb) {
+  const float4 b0 = __ldg(reinterpret_cast<const float4 *>(p));
+  const float4 b1 = __ldg(reinterpret_cast<const float4 *>(p + 4));
+  bb[0] = b0.x; bb[1] = b0.y; bb[2] = b0.z; bb[3] = b0.w;
+  bb[4] = b1.x; bb[5] = b1.y; bb[6] = b1.z; bb[7] = b1.w;
+}
+
+// epilogue32 for 8 channels n .. n+7 of one pixel; bias8 (forward, optional): their bias,
+// already in registers
 __device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g, int b, int y,
-                                          int x, int n, float *v) {
+                                          int x, int n, float *v, const float *bias8 = nullptr) {
   const bool valid = y < (g.eh >> a.level) && x < (g.ew >> a.level);
   const size_t o = (((size_t)b * a.Hb + y) * a.Wb + x) * a.cout + n;
   if (a.mode == kEpiForward) {
-    const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n));
-    const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + 4));
-    const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float bb[8];
+    if (bias8) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) bb[j] = bias8[j];
+    } else {
+      load8_bias(a.bias + n, bb);
+    }
 #pragma unroll
     for (int j = 0; j < 8; j++) v[j] = valid ? fmaxf(v[j] + bb[j], 0.f) : 0.f;
   } else if (!valid) {
@@ -324,7 +337,7 @@ __device__ __forceinline__ void epilogue8(const ConvArgs &a, const BlockGeom &g,
 // decided on those FP32 values, and the max is rounded once to BF16 for the pooled map
 __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g, int b,
                                            int oy, int ox, const TcGeom &tg, int c, int n,
-                                           const uint8_t *tsm) {
+                                           const uint8_t *tsm, const float *bias8 = nullptr) {
   const int lane = threadIdx.x & 31;
   const int w = lane >> 2, cg = lane & 3;
   const int wpr = tg.TW >> 1;   // windows per row pair
@@ -332,9 +345,13 @@ __device__ __forceinline__ void swap_pool8(const ConvArgs &a, const BlockGeom &g
   const int pp0 = c + j0;
   const int y = oy + pp0 / tg.TW, x = ox + pp0 % tg.TW;
   if (pp0 >= tg.TH * tg.TW || y >= a.Hb || x >= a.Wb) return;
-  const float4 b0 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8));
-  const float4 b1 = __ldg(reinterpret_cast<const float4 *>(a.bias + n + cg * 8 + 4));
-  const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  float bb[8];
+  if (bias8) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) bb[j] = bias8[j];
+  } else {
+    load8_bias(a.bias + n + cg * 8, bb);
+  }
   const int ehl = g.eh >> a.level, ewl = g.ew >> a.level;
   float m[8];
   int k8[8];   // window position (row-major) of the first maximum
@@ -960,6 +977,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;            // TMEM lane quarter = channels q*32 .. q*32+31 of the tile
     const int half = (warp - 2) >> 2;  // pixels half*128 .. half*128+127 of the patch
     uint8_t *tsm = smem_gen + STAGES * STAGE_BYTES + (size_t)(warp - 2) * kTileT;
+    // forward with one channel tile: this thread's 8 channels (q * 32 + 8 (lane % 4)) are the
+    // same on every tile, so their bias is loaded once
+    float sbias[8];
+    const bool hoist = a.mode == kEpiForward && tg.n_tiles == 1;
+    if (hoist) load8_bias(a.bias + q * 32 + (lane & 3) * 8, sbias);
     int it = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
@@ -996,9 +1018,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           swap_tile_read8(tsm, j, cg, r);
           const int pp = c + j;
           const int y = oy + pp / tg.TW, x = ox + pp % tg.TW;
-          if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb) epilogue8(a, g, b, y, x, n + cg * 8, r);
+          if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb)
+            epilogue8(a, g, b, y, x, n + cg * 8, r, hoist ? sbias : nullptr);
         }
-        if (a.pool_out) swap_pool8(a, g, b, oy, ox, tg, c, n, tsm);
+        if (a.pool_out) swap_pool8(a, g, b, oy, ox, tg, c, n, tsm, hoist ? sbias : nullptr);
         __syncwarp();
       }
       tc_fence_before();
@@ -1142,6 +1165,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - 2) >> 2;  // pixels half*128 .. half*128+127 of the patch
     uint8_t *tsm = smem_gen + kSHBoxStages * kSHBoxStage + kSHWStages * kSHWTile +
                    (size_t)(warp - 2) * kTileT;
+    float sbias[8];   // (forward) this thread's 8 channels' bias, the same on every tile
+    const bool hoist = a.mode == kEpiForward;
+    if (hoist) load8_bias(a.bias + q * 32 + (lane & 3) * 8, sbias);
     int it = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, it++) {
       const int acc = it & 1;
@@ -1172,7 +1198,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           swap_tile_read8(tsm, j, cg, r);
           const int pp = c + j;
           const int y = oy + pp / kSHTW, x = ox + pp % kSHTW;
-          if (y < a.Hb && x < a.Wb) epilogue8(a, g, b, y, x, n + cg * 8, r);
+          if (y < a.Hb && x < a.Wb)
+            epilogue8(a, g, b, y, x, n + cg * 8, r, hoist ? sbias : nullptr);
         }
         __syncwarp();
       }

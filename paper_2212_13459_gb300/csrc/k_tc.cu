@@ -527,6 +527,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           *reinterpret_cast<float4 *>(tsm + lane * 128 + ((k ^ (lane & 7)) << 4)) =
               make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
         __syncwarp();
+        float cbias[8];   // (forward) the bias of this thread's 8 channels of the chunk
+        if (a.mode == kEpiForward) load8_bias(a.bias + nt * BN + c + cg * 8, cbias);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
           const int j = k * 8 + (lane >> 2);
@@ -535,7 +537,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (pp < tg.TH * tg.TW && y < a.Hb && x < a.Wb) {
             float r[8];
             swap_tile_read8(tsm, j, cg, r);
-            epilogue8(a, g, b, y, x, nt * BN + c + cg * 8, r);
+            epilogue8(a, g, b, y, x, nt * BN + c + cg * 8, r,
+                      a.mode == kEpiForward ? cbias : nullptr);
           }
         }
         if (a.pool_out) swap_pool8(a, g, b, oy, ox, tg, q * 32, nt * BN + c, tsm);

@@ -770,12 +770,24 @@ __global__ void __launch_bounds__(256) chansum_partial_kernel(
   }
 }
 
-__global__ void chansum_reduce_kernel(const double *__restrict__ partial, int nchunks, int C,
-                                      double *__restrict__ S) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < nchunks; c++) s += partial[(size_t)c * C + j];
-    S[j] += s;
+// S[j] += sum over chunks of partial[c][j]: a CTA takes 32 channels (lane = channel), its 8 warps
+// split the chunks (warp w: chunks w, w + 8, ... in order), then the warps are added in order
+__global__ void __launch_bounds__(256) chansum_reduce_kernel(const double *__restrict__ partial,
+                                                             int nchunks, int C,
+                                                             double *__restrict__ S) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (j < C)
+    for (int c = warp; c < nchunks; c += 8) s += partial[(size_t)c * C + j];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && j < C) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) t += red[w][lane];
+    S[j] += t;
   }
 }
 
@@ -785,7 +797,7 @@ void launch_chansum(const T *V, int Hb, int Wb, int C, const OwnRect *own,
                     cudaStream_t s) {
   if (nchunks <= 0) return;
   chansum_partial_kernel<T><<<nchunks, 256, 0, s>>>(V, Hb, Wb, C, own, chunks, partial);
-  chansum_reduce_kernel<<<(C + 255) / 256, 256, 0, s>>>(partial, nchunks, C, S);
+  chansum_reduce_kernel<<<(C + 31) / 32, 256, 0, s>>>(partial, nchunks, C, S);
 }
 template void launch_chansum<float>(const float *, int, int, int, const OwnRect *,
                                     const GramChunk *, int, double *, double *, cudaStream_t);
